@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs for the Born solver (media, sources, grid units).
+
+This module only builds inputs: sound speed c0 (m/s), density rho (kg/m^3),
+absorption alpha (Np/m), grid step, angular frequency, absorbing-layer
+parameters and sources.  It holds none of the solver's arithmetic, so both the
+CUDA path and the FP64 CPU oracle can take their inputs from it.
+
+Units (the paper's experiments run at 500 kHz in water, Sec. 3):
+  f = 500 kHz, background c = 1500 m/s, grid step dx = c_bg / (f * PPW),
+  alpha [Np/m] = alpha0 [dB/cm/MHz] * f[MHz] * 100 / (20 log10 e)
+  (linear frequency power law).
+Absorbing layer: n_abs cells inside the grid on every side, quadratic profile,
+gamma_max = 3 c_ref ln(1/R) / (2 n_abs dx) with R = 1e-4, the nominal
+normal-incidence round-trip reflection of a quadratic layer.
+
+Arrays are numpy float64 with shape (n[D-1], ..., n[0]) (x fastest).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+F0 = 5.0e5
+C_WATER = 1500.0
+RHO_WATER = 1000.0
+NEPER_PER_DB = 1.0 / (20.0 * math.log10(math.e))
+
+
+def db_cm_mhz_to_np_m(alpha0: float, f_hz: float = F0) -> float:
+    """Absorption in dB/(cm MHz) -> Np/m at frequency f (linear power law)."""
+    return alpha0 * (f_hz / 1e6) * 100.0 * NEPER_PER_DB
+
+
+def grid_step(ppw: float, f_hz: float = F0, c_bg: float = C_WATER) -> float:
+    return c_bg / (f_hz * ppw)
+
+
+def layer_gamma_max(n_abs: int, dx: float, c_ref: float = C_WATER, refl: float = 1e-4) -> float:
+    """Peak absorption of a quadratic layer of n_abs cells with round-trip reflection ``refl``."""
+    return 3.0 * c_ref * math.log(1.0 / refl) / (2.0 * n_abs * dx)
+
+
+@dataclass
+class Problem:
+    """One solve's inputs.  ``source`` has shape (D+1, *shape): (s_u..., s_p)."""
+
+    name: str
+    c0: np.ndarray
+    rho: np.ndarray
+    alpha: np.ndarray
+    dx: float
+    omega: float
+    nabs: list
+    gamma_max: float
+    power: float = 2.0
+    source: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return self.c0.shape
+
+    @property
+    def ndim(self):
+        return self.c0.ndim
+
+    @property
+    def n_voxels(self):
+        return int(np.prod(self.c0.shape))
+
+
+def _centre_dist(shape, centre):
+    grids = np.meshgrid(*[np.arange(s, dtype=np.float64) for s in shape], indexing="ij")
+    # grids are in numpy axis order (..., y, x); centre is given in (x, y, z) order
+    r2 = np.zeros(shape)
+    for ax in range(len(shape)):
+        r2 += (grids[ax] - centre[len(shape) - 1 - ax]) ** 2
+    return np.sqrt(r2)
+
+
+def inclusion_medium(shape, radius, c_in, rho_in, alpha_in_db, centre=None, ppw=6.0, n_abs=16,
+                     f_hz=F0, c_bg=C_WATER, rho_bg=RHO_WATER):
+    """Water with one centred disc (2D) or sphere (3D); inside = cell-centre distance < radius."""
+    if centre is None:
+        centre = tuple(s // 2 for s in shape[::-1])
+    dx = grid_step(ppw, f_hz, c_bg)
+    r = _centre_dist(shape, centre)
+    inside = r < radius
+    c0 = np.where(inside, c_in, c_bg).astype(np.float64)
+    rho = np.where(inside, rho_in, rho_bg).astype(np.float64)
+    alpha = np.where(inside, db_cm_mhz_to_np_m(alpha_in_db, f_hz), 0.0).astype(np.float64)
+    nabs = [[n_abs, n_abs] for _ in shape]
+    return Problem(name="inclusion", c0=c0, rho=rho, alpha=alpha, dx=dx, omega=2 * math.pi * f_hz, nabs=nabs,
+                   gamma_max=layer_gamma_max(n_abs, dx, c_bg) if n_abs > 0 else 0.0,
+                   meta=dict(radius=radius, centre=centre, c_in=c_in, rho_in=rho_in,
+                             alpha_in=db_cm_mhz_to_np_m(alpha_in_db, f_hz), c_bg=c_bg, rho_bg=rho_bg, ppw=ppw,
+                             n_abs=n_abs, f=f_hz))
+
+
+def point_source(shape, pos_xyz, amplitude=1.0 + 0j):
+    """Single-voxel pressure source s_p at cell pos (x, y, z order); zero velocity sources."""
+    src = np.zeros((len(shape) + 1,) + tuple(shape), dtype=np.complex128)
+    idx = tuple(pos_xyz[::-1])
+    src[(len(shape),) + idx] = amplitude
+    return src
+
+
+def disc_128():
+    """2D 128x128: water, disc radius 20 cells (c 2500, rho 1800, 1 dB/cm/MHz), 6 PPW, 16-cell layer."""
+    p = inclusion_medium((128, 128), 20, 2500.0, 1800.0, 1.0, ppw=6.0, n_abs=16)
+    p.name = "disc2d_128"
+    return p
+
+
+def sphere_128(n=128, radius=24, n_abs=20, src_offset=10):
+    """3D n^3: water, sphere radius 24 (c 2200, rho 1600, 2 dB/cm/MHz), 6 PPW, 20-cell layer, point source
+    ``src_offset`` cells inside the layer's inner edge on the -x side, on the sphere's axis."""
+    shape = (n, n, n)
+    p = inclusion_medium(shape, radius, 2200.0, 1600.0, 2.0, ppw=6.0, n_abs=n_abs)
+    c = p.meta["centre"]
+    pos = (n_abs + src_offset, c[1], c[2])
+    p.source = point_source(shape, pos)
+    p.meta["source_pos"] = pos
+    p.name = f"sphere3d_{n}"
+    return p
+
+
+def smooth_random_medium(shape, seed, c_range=(1400.0, 2800.0), rho_range=(900.0, 1900.0),
+                         alpha_db_range=(0.0, 5.0), sigma_frac=1.0 / 16, ppw=6.0, n_abs=16, f_hz=F0):
+    """Uniform noise smoothed by a periodic Gaussian (sigma = sigma_frac * n), affinely mapped to ranges."""
+    rng = np.random.default_rng(seed)
+
+    def smooth():
+        a = rng.random(shape)
+        A = np.fft.fftn(a)
+        g = np.ones(shape)
+        for ax, n in enumerate(shape):
+            k = np.fft.fftfreq(n)
+            s = sigma_frac * n
+            sh = [1] * len(shape)
+            sh[ax] = n
+            g = g * np.exp(-2.0 * (math.pi * k * s) ** 2).reshape(sh)
+        b = np.real(np.fft.ifftn(A * g))
+        lo, hi = b.min(), b.max()
+        return (b - lo) / (hi - lo if hi > lo else 1.0)
+
+    c0 = c_range[0] + (c_range[1] - c_range[0]) * smooth()
+    rho = rho_range[0] + (rho_range[1] - rho_range[0]) * smooth()
+    al = alpha_db_range[0] + (alpha_db_range[1] - alpha_db_range[0]) * smooth()
+    alpha = al * db_cm_mhz_to_np_m(1.0, f_hz)
+    dx = grid_step(ppw, f_hz)
+    nabs = [[n_abs, n_abs] for _ in shape]
+    return Problem(name=f"random{len(shape)}d", c0=c0, rho=rho, alpha=alpha, dx=dx, omega=2 * math.pi * f_hz,
+                   nabs=nabs, gamma_max=layer_gamma_max(n_abs, dx) if n_abs > 0 else 0.0, meta=dict(seed=seed))
+
+
+def random_source(shape, seed, velocity=True):
+    """Dense complex Gaussian source in every component (parity-test input)."""
+    rng = np.random.default_rng(seed)
+    s = rng.standard_normal((len(shape) + 1,) + tuple(shape)) + 1j * rng.standard_normal((len(shape) + 1,) + tuple(shape))
+    if not velocity:
+        s[:-1] = 0
+    return s
