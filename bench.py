@@ -1,0 +1,314 @@
+"""Benchmark of the split-preconditioned Born solver on one GB300.
+
+Workload (one "step" = one full solve through every step of the hot path):
+3D 128^3 grid, water (c 1500 m/s, rho 1000 kg/m^3) with a centred fluid sphere
+of radius 24 cells (c 2200, rho 1600, 2 dB/cm/MHz), 500 kHz, 6 points per
+wavelength, 20-cell absorbing layer, single-voxel pressure source 10 cells
+inside the layer's inner edge; solved to a relative scaled residual of 1e-6.
+A step is set-up (complex sound speed, staggered density, shifts, scaling),
+the Born iterations, the float64 residual checks / refinement and the output
+scaling, with the medium and source already resident on the device.
+
+Metric: voxel-iterations per second (N_v * Born iterations / step time) of
+the FP32 + FP64-refinement path; time to the 1e-6 residual for it and for the
+plain FP64 path side by side.  --impl reference times the FP64 CPU oracle on
+the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iters/s & time-to-1e-6 residual, FP32+refine vs FP64; p50/p99 latency"
+UNIT = "voxel-iter/s"
+WORKLOAD = "sphere3d_128: 128^3, sphere r=24 (c 2200, rho 1600, 2 dB/cm/MHz), point source, 20-cell layer, 6 PPW, tol 1e-6"
+TOL = 1e-6
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.lines = []
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+# ------------------------------------------------------------------ oracle arm
+def cpu_oracle_rate(problem, n_iter=1):
+    """Voxel-iterations/s of the FP64 CPU oracle on the host cores (bounded sample)."""
+    from oracle import oracle as O
+
+    P = O.Problem(problem.c0, problem.rho, problem.alpha, problem.dx, problem.omega, problem.nabs,
+                  problem.gamma_max)
+    y = P.scale_source(problem.source)
+    t0 = time.perf_counter()
+    P.iterate(y, n_iter=n_iter, nu=0.5)
+    dt = time.perf_counter() - t0
+    return problem.n_voxels * n_iter / dt, dt, O.max_threads()
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    from paper_2507_16087_gb300 import workloads as W
+
+    p = W.sphere_128()
+    rates = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(p, 1)
+    t_all = 0.0
+    for _ in range(args.steps):
+        r, dt, cores = cpu_oracle_rate(p, 1)
+        rates.append(r)
+        t_all += dt
+    value = float(p.n_voxels * args.steps / t_all)
+    sample = f"{args.steps} x 1 FP64 Born iteration of the 128^3 sphere workload (own FFT, OpenMP)"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------- GPU arm
+def kernel_bytes_per_voxel(D=3, fp=4):
+    """Algorithmic bytes per voxel of each kernel of one iteration (reads + writes of fields and medium)."""
+    C = D + 1
+    cb = 2 * fp               # one complex value
+    medium = D * fp + 2 * fp  # rs_eta per velocity component + (kp, et) for pressure
+    return {"rows_fwd": C * cb * 3 + medium,   # x, y in; w out
+            "axis_fwd": C * cb * 2, "last_symbol": C * cb * 2, "axis_inv": C * cb * 2,
+            "rows_inv": C * cb * 3 + medium,   # w, x in; x out
+            "reduce": 0}
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2507_16087_gb300 import cbs, workloads as W
+
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = W.sphere_128()
+    Nv = p.n_voxels
+    T = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    c0, rho, al = T(p.c0), T(p.rho), T(p.alpha)
+    src = T(p.source, torch.complex128)
+    field = torch.zeros((4,) + p.shape, dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    kw = dict(tol=TOL, check_every=args.check_every, tol_inner=args.tol_inner)
+
+    def solve(precision):
+        s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision=precision, **kw)
+        info = s.solve_forward(src, field)
+        s.destroy()
+        return info
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        solve("fp32_refine")
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    times, iters, launches, infos = [], [], 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = solve("fp32_refine")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        times.append(e0.elapsed_time(e1))
+        iters.append(info["iters"])
+        launches += info["kernel_launches"]
+        infos.append(info)
+    clk = clocks.stop()
+    t_ms = np.array(times)
+    step_ms = float(t_ms.mean())
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    value = ws * Nv * float(np.mean(iters)) / (step_ms / 1e3)
+
+    # plain FP64 side by side (one warm-up, one timed)
+    fp64 = None
+    if not args.no_fp64:
+        solve("fp64")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i64 = solve("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        fp64 = {"time_to_1e-6_ms": t64, "iters": i64["iters"], "rel_residual": i64["rel_residual"],
+                "voxel_iters_per_s": Nv * i64["iters"] / (t64 / 1e3)}
+
+    # per-kernel times (CUDA events on the solver's stream) for the roofline
+    s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision="fp32_refine", **kw)
+    y = torch.zeros_like(field)
+    s.scale_source(src, y)
+    x = torch.zeros_like(field)
+    kt = s.time_kernels(y, x, 5)
+    kt = s.time_kernels(y, x, 20)
+    s.destroy()
+    bpv = kernel_bytes_per_voxel(3, 4)
+    peak, peak_kind = _peaks()
+    top = max((k for k in kt if bpv.get(k, 0) > 0), key=lambda k: kt[k])
+    achieved = bpv[top] * Nv / (kt[top] / 1e3) / 1e9
+    iter_ms = sum(kt.values())
+    roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "bytes_per_voxel": bpv[top], "kernel_ms": kt,
+            "iteration_ms": iter_ms,
+            "iteration_frac": sum(bpv.values()) * Nv / (iter_ms / 1e3) / 1e9 / peak}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    hc = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.c0, p.rho, p.alpha)]
+    hs = torch.from_numpy(np.ascontiguousarray(p.source)).pin_memory()
+    hout = torch.empty((4,) + p.shape, dtype=torch.complex128).pin_memory()
+    e2e_t = []
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dc = [a.to(dev, non_blocking=True) for a in hc]
+        ds = hs.to(dev, non_blocking=True)
+        fld = torch.empty((4,) + p.shape, dtype=torch.complex128, device=dev)
+        s = cbs.solver_create(dc[0], dc[1], dc[2], p.dx, p.omega, p.nabs, p.gamma_max, precision="fp32_refine", **kw)
+        ie = s.solve_forward(ds, fld)
+        hout.copy_(fld, non_blocking=True)
+        torch.cuda.synchronize()
+        s.destroy()
+        e2e_t.append(time.perf_counter() - t0)
+    h2d = sum(a.numel() * a.element_size() for a in hc) + hs.numel() * hs.element_size()
+    d2h = hout.numel() * hout.element_size()
+    e2e = {"value": Nv * ie["iters"] / e2e_t[-1], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "time_to_1e-6_ms": 1e3 * e2e_t[-1]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, dt, cores = cpu_oracle_rate(p, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"1 FP64 Born iteration of the same 128^3 workload ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64 inner / f64 refine", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": "fp32_refine", "l2": "flushed (256 MB write) between steps",
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "time_to_1e-6_ms": step_ms, "iters": float(np.mean(iters)),
+                "outer_iters": infos[-1]["outer_iters"], "rel_residual": infos[-1]["rel_residual"],
+                "setup_ms": infos[-1]["t_setup_ms"], "fp64": fp64, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--check-every", type=int, default=50)
+    ap.add_argument("--tol-inner", type=float, default=1e-4)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

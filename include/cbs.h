@@ -1,0 +1,176 @@
+/*
+ * cbs.h -- C ABI of the GB300 Born solver for the acoustic Helmholtz equation
+ * with heterogeneous sound speed, density and absorption.
+ *
+ * Method: A. Stanziola, S. R. Arridge, B. E. Treeby, B. T. Cox, "Iterative
+ * Born solver for the acoustic Helmholtz equation with heterogeneous sound
+ * speed and density" (arXiv 2507.16087).  The solver iterates eq. BornAlt
+ * (Algorithm 1) on the row-scaled first-order system (eq. HH1stOrderSH) on a
+ * staggered grid (App. B.1):
+ *
+ *   [ (S+ rho)(S+ gamma + i omega)   S+ grad            ] [ u ]   [ (S+ rho) s_u     ]
+ *   [ div S-                         (i omega + gamma)/(rho c^2) ] [ p ] = [ s_p / (rho c^2) ]
+ *
+ * with the complex sound speed c^2 = c0^2 / (1 - 2 i alpha c0 / omega)
+ * (eq. 118), split A = L + V with shifts a1, a2 and scaling C = diag(lambda1,
+ * lambda2) (eq. LV, eq. C), and (L+I)^-1 applied in the Fourier domain
+ * (App. B.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Grid: ndim = 2 or 3, extents n[0] (x, fastest), n[1] (y), n[2] (z);
+ *    every extent is one of 8,12,16,24,32,48,64,96,128,192,256,512.
+ *  - Field / source arrays: caller-owned DEVICE buffers of (ndim+1)*N
+ *    complex128 values (interleaved re, im; 16-byte aligned), component-major
+ *    [u_x][u_y][(u_z)][p], each component laid out [n2][n1][n0].  Velocity
+ *    component eta sits at the staggered points x + (dx/2) e_eta.
+ *  - Medium arrays c0 (m/s), rho (kg/m^3), alpha (Np/m): caller-owned DEVICE
+ *    buffers of N float64 values [n2][n1][n0].  They are read during
+ *    solver_create only; the solver keeps its own derived copies.
+ *  - Every call enqueues its work on the solver's internal stream after the
+ *    work already queued on opt->stream, and returns only when its work is
+ *    complete.  Results (info, scalars) are valid on return.
+ *  - Errors are return codes; cbs_last_error gives a message.  Nothing aborts,
+ *    exits or throws across the ABI.  A call with invalid arguments changes no
+ *    output.
+ */
+#ifndef CBS_H
+#define CBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CBS_OK = 0,
+    CBS_EINVAL = 1,     /* invalid argument, unsupported size, rejected medium */
+    CBS_ENOMEM = 2,     /* device allocation failed */
+    CBS_ECUDA = 3,      /* a CUDA call failed */
+    CBS_ENOCONV = 4,    /* max_iter reached before tol; field holds the last iterate */
+    CBS_EDIVERGED = 5,  /* non-finite or growing iterate; field holds the last finite iterate */
+    CBS_ETIMEOUT = 6    /* reserved */
+} cbs_status;
+
+enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1, CBS_FP32 = 2 };
+enum { CBS_SHIFT_MIDRANGE = 0, CBS_SHIFT_MEDIAN = 1 };
+
+typedef struct {
+    int ndim;      /* 2 or 3 */
+    int64_t n[3];  /* n[0] = x (fastest) .. n[ndim-1]; unused entries ignored */
+} cbs_grid;
+
+/* Absorbing layer gamma(x) (the paper names it, Sec. 2.1, but gives no
+ * profile): n_abs[a][0/1] cells on the low/high side of axis a, inside the
+ * grid; depth(xi) = min(1, max(0, (lo - xi)/lo, (xi - (n-1-hi))/hi)) at cell
+ * coordinate xi; gamma = gamma_max * sum_a depth_a^power; the staggered
+ * values are taken at xi + 1/2 (App. B.1). */
+typedef struct {
+    int n_abs[3][2];
+    double gamma_max; /* 1/s */
+    double power;
+} cbs_boundary;
+
+typedef struct {
+    int precision;     /* CBS_FP64 (default), CBS_FP32_REFINE, CBS_FP32 */
+    double nu;         /* 0 < nu < 1 (eq. BornAlt); 0 -> 0.5 */
+    double beta;       /* 0 < beta < 1 (eq. C); 0 -> 0.95 */
+    int shift_rule;    /* CBS_SHIFT_MIDRANGE (default) or CBS_SHIFT_MEDIAN */
+    double tol;        /* relative scaled residual ||y - A_s x|| / ||y||; <= 0: run exactly max_iter */
+    double tol_inner;  /* FP32_REFINE: inner relative reduction per outer step; 0 -> 1e-4 */
+    int max_iter;      /* Born iterations (all inner iterations for FP32_REFINE); 0 -> 100000 */
+    int check_every;   /* iterations between residual checks; 0 -> 50 */
+    void* stream;      /* cudaStream_t the caller's work is queued on (may be 0) */
+} cbs_options;
+
+typedef struct {
+    int iters;              /* Born iterations run (FP32 inner iterations for FP32_REFINE) */
+    int outer_iters;        /* refinement steps (FP32_REFINE), else 0 */
+    int residual_checks;    /* true-residual evaluations */
+    double rel_residual;    /* last true scaled residual (FP64 for FP64 and FP32_REFINE) */
+    double rel_increment;   /* last ||x_{k+1} - x_k|| / ||x_{k+1}|| (Algorithm 1's criterion) */
+    double a1[2], a2[2];    /* shifts (re, im) */
+    double lambda1, lambda2;/* scaling (eq. C) */
+    double t_setup_ms;      /* solver_create device time */
+    double t_solve_ms;      /* this call's device time */
+    long long kernel_launches; /* kernels this call launched (graph nodes included) */
+} cbs_info;
+
+typedef struct cbs_solver cbs_solver;
+
+/* Build a solver for one medium, frequency and grid (Algorithm 1
+ * preprocessing): complex sound speed (eq. 118), staggered density
+ * (App. B.1), diagonal values, shifts a1, a2 (midrange of the diagonal values
+ * by default; componentwise median on request), lambda_j = max|diag - a_j| /
+ * beta (eq. C; lambda_j = |a_j| when that max is 0), per-axis wavenumber and
+ * twiddle tables.  c0, rho, alpha: device float64 [N].  Rejects (CBS_EINVAL)
+ * non-finite values, c0 <= 0, rho <= 0, alpha < 0, unsupported extents,
+ * nu/beta outside (0,1).  On success *out owns all device memory it uses until
+ * solver_destroy. */
+cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const double* c0, const double* rho,
+                         const double* alpha, const cbs_boundary* boundary, const cbs_options* opt,
+                         cbs_solver** out);
+
+/* Solve A (u, p) = (S+ rho s_u, s_p / (rho c^2)) for the physical field
+ * (Algorithm 1: x = 0 or x0, iterate, output C^-1/2 x).  src, field: device
+ * complex128 [C][N] (physical s_u, s_p in; physical u, p out).  x0_or_null:
+ * optional physical start field.  Stops when the true scaled residual
+ * ||y - A_s x|| / ||y|| <= tol (checked every check_every iterations); FP64:
+ * all arithmetic in float64; FP32_REFINE: inner Born iterations in float32 on
+ * r / ||r|| with the residual r = y - A_s x, its norm and the correction
+ * accumulation in float64; FP32: everything in float32 (residual in float32).
+ * info may be NULL. */
+cbs_status solve_forward(cbs_solver* s, const void* src, void* field, const void* x0_or_null, cbs_info* info);
+
+/* Solve the adjoint system A^H lambda = g (Sec. 2.3: A^H is accretive for
+ * alpha >= 0, so the same iteration applies with conj(B) and the per-wavenumber
+ * conjugate transpose of the staggered (L+I)^-1 symbol).  g is taken as the
+ * adjoint right-hand side as given (no row scaling).  Same layouts and stopping
+ * rule as solve_forward. */
+cbs_status solve_adjoint(cbs_solver* s, const void* src, void* field, const void* x0_or_null, cbs_info* info);
+
+/* Relative scaled residual of a physical field for a physical source,
+ * ||y - A_s C^1/2 (u,p)|| / ||y|| with y the scaled source (adjoint != 0: the
+ * adjoint system), computed in float64 on the device. */
+cbs_status residual_norm(cbs_solver* s, const void* field, const void* src, int adjoint, double* rel);
+
+/* Run exactly n_iter Born iterations (eq. BornAlt) in the solver's precision
+ * (FP64, or FP32 for FP32 / FP32_REFINE) on the scaled variables, starting from
+ * the scaled iterate x (device complex128 [C][N], updated in place) with the
+ * scaled right-hand side y (device complex128).  incr (host, n_iter doubles,
+ * may be NULL) receives ||x_{k+1}-x_k|| / ||x_{k+1}|| per iteration. */
+cbs_status born_iterate(cbs_solver* s, const void* y, void* x, int n_iter, int adjoint, double* incr);
+
+/* out = (L+I)^-1 in (adjoint: [(L+I)^-1]^H in) on scaled fields (device
+ * complex128 [C][N]), in the solver's iteration precision (App. B.1). */
+cbs_status green_apply(cbs_solver* s, const void* in, void* out, int adjoint);
+
+/* out = A_s x = L x + V x (adjoint: A_s^H x) on scaled fields, float64 (eq. LV). */
+cbs_status operator_apply(cbs_solver* s, const void* x, void* out, int adjoint);
+
+/* y = C^-1/2 (S+ rho s_u, s_p / (rho c^2))  (adjoint: y = C^-1/2 g), and the
+ * inverse map field = C^-1/2 x of Algorithm 1's output.  Device complex128. */
+cbs_status scale_source(cbs_solver* s, const void* src, void* y, int adjoint);
+cbs_status unscale_field(cbs_solver* s, const void* x, void* field);
+
+/* Shifts and scaling: out[0..5] = Re a1, Im a1, Re a2, Im a2, lambda1, lambda2. */
+cbs_status solver_scalars(const cbs_solver* s, double* out);
+
+/* Average device time (ms) per launch of each kernel of one Born iteration,
+ * measured with CUDA events on the solver's stream over n_iter iterations
+ * (scaled iterate and source taken as given, updated in place).  names
+ * receives up to max_k NUL-separated kernel names; ms receives one time per
+ * kernel; *nk the kernel count. */
+cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter, char* names, int names_len,
+                               double* ms, int max_k, int* nk);
+
+void solver_destroy(cbs_solver* s);
+
+/* Message of the last failure on this solver (or of the last failed
+ * solver_create when s is NULL).  Never NULL. */
+const char* cbs_last_error(const cbs_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBS_H */

@@ -1,0 +1,404 @@
+// born.cuh -- fused kernels of the split-preconditioned Born iteration.
+//
+// One iteration of eq. BornAlt / Algorithm 1 (Stanziola et al.),
+//     z = (L+I)^-1 (B x + y),   x <- x + nu B (z - x),   B = I - V,
+// on a D-dim grid (D = 2, 3) with C = D+1 components, runs as
+//     rows_fwd     w = B x + y, forward FFT along x               (per row)
+//     axis_fft     forward FFT along y (3D only)                  (per y-pencil tile)
+//     last_symbol  forward FFT along the last axis, the per-wavenumber
+//                  (L+I)^-1 symbol of App. B.1 on all C components,
+//                  inverse FFT along the last axis                (per pencil tile)
+//     axis_fft     inverse FFT along y (3D only)
+//     rows_inv     inverse FFT along x, update of x, norm partials (per row)
+// The same kernels with other modes give the scaled operator A_s x = L x + V x
+// (residual y - A_s x) and the adjoint (A_s^H, conj(B), [(L+I)^-1]^H).
+//
+// Field layout: [C][n2][n1][n0] interleaved complex, x fastest.
+// Medium layout: rs[eta][N] = (S+ rho)_eta / lambda1, kp[N] = 1/(rho c0^2 lambda2),
+// et[N] = 2 alpha c0 / omega; gamma from per-axis tables at centres (gc) and
+// at the staggered points (gs).  V is never stored: per voxel
+//   v_eta = rs_eta * gamma_eta - a1/lambda1 + i (rs_eta omega)    ... minus i Im(a1)/lambda1
+//   v_p   = kp [(gamma + et omega) + i (omega - gamma et)] - a2/lambda2
+// (eq. LV with q = (i omega + gamma)/(rho c^2), c^2 of eq. 118).
+#pragma once
+#include "fft.cuh"
+
+namespace cbs {
+
+enum RowsFwdMode { FWD_BORN = 0, FWD_COPY = 1 };
+enum RowsInvMode { INV_BORN = 0, INV_RESID = 1, INV_PLAIN = 2, INV_APPLY = 3 };
+enum SymbolMode { SYM_GREEN = 0, SYM_GREEN_ADJ = 1, SYM_L = 2, SYM_L_ADJ = 3 };
+
+struct Dims {
+    int D;          // 2 or 3
+    int n0, n1, n2; // extents (n2 = 1 in 2D)
+    long long N;    // voxels
+};
+
+template <typename R> struct Medium {
+    const R* rs[3];
+    const R* kp;
+    const R* et;
+    const R* gc[3];
+    const R* gs[3];
+    R omega;
+    R a1r, a1i, a2r, a2i;  // a_j / lambda_j
+};
+
+template <typename R> struct Symbol {
+    cplx<R> P;     // lambda1 / (a1 + lambda1) * scale
+    cplx<R> Pu;    // lambda1 / (a1 + lambda1)
+    cplx<R> c1;    // i sqrt(lambda1 lambda2)
+    cplx<R> c2;    // lambda2 (a1 + lambda1)
+    cplx<R> c3;    // (a1 + lambda1)(a2 + lambda2)
+    cplx<R> la1;   // a1 / lambda1
+    cplx<R> la2;   // a2 / lambda2
+    R isq;         // 1 / sqrt(lambda1 lambda2)
+    R scale;       // 1 / N (inverse-transform normalisation)
+    const cplx<R>* kt[3];  // t_eta = k_eta exp(i k_eta dx / 2)
+    const R* k2[3];        // k_eta^2
+};
+
+// Per-row view of B = 1 - v for component c (conj for the adjoint).  Along a
+// row only x varies, so the gamma terms of the other axes are row constants.
+template <typename R> struct RowB {
+    const R* g0;  // gamma along x: staggered table for u_x, centre table otherwise
+    R grest;      // gamma contributions of y (and z)
+    const R* m0;  // rs_c (velocity) or kp (pressure), at the row start
+    const R* m1;  // et (pressure), at the row start
+    bool pres;
+};
+
+template <typename R>
+__device__ __forceinline__ RowB<R> row_B(const Medium<R>& M, int D, int c, int i1, int i2, long long vbase)
+{
+    RowB<R> rb;
+    rb.pres = (c == D);
+    rb.g0 = (c == 0) ? M.gs[0] : M.gc[0];
+    R g = (c == 1) ? __ldg(M.gs[1] + i1) : __ldg(M.gc[1] + i1);
+    if (D == 3) g += (c == 2) ? __ldg(M.gs[2] + i2) : __ldg(M.gc[2] + i2);
+    rb.grest = g;
+    const R* rsc = (c == 0) ? M.rs[0] : ((c == 1) ? M.rs[1] : M.rs[2]);
+    rb.m0 = (rb.pres ? M.kp : rsc) + vbase;
+    rb.m1 = M.et + vbase;
+    return rb;
+}
+
+template <typename R>
+__device__ __forceinline__ cplx<R> born_B(const Medium<R>& M, const RowB<R>& rb, int i0, bool adj)
+{
+    const R g = __ldg(rb.g0 + i0) + rb.grest;
+    R vr, vi;
+    if (!rb.pres) {
+        const R r = __ldg(rb.m0 + i0);
+        vr = r * g - M.a1r;
+        vi = r * M.omega - M.a1i;
+    } else {
+        const R k = __ldg(rb.m0 + i0), e = __ldg(rb.m1 + i0);
+        vr = k * (g + e * M.omega) - M.a2r;
+        vi = k * (M.omega - g * e) - M.a2i;
+    }
+    return mk<cplx<R>, R>((R)1 - vr, adj ? vi : -vi);
+}
+
+template <int T> struct RowSync {
+    __device__ __forceinline__ void operator()() const
+    {
+        if constexpr (T <= 32) __syncwarp();
+        else __syncthreads();
+    }
+};
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Block-wide sum of two doubles; thread 0 writes them to out[0..1].
+__device__ __forceinline__ void block_sum2(double a, double b, double* out)
+{
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { red[0][w] = a; red[1][w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = lane < nw ? red[0][lane] : 0.0;
+        b = lane < nw ? red[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) { out[0] = a; out[1] = b; }
+    }
+}
+
+// Rows of one block: 256 threads when the rows' shared memory fits in 32 KiB.
+template <typename R, int NX, int RX> struct RowCfg {
+    static constexpr int T = NX / RX;
+    static constexpr int ROWS0 = (T >= 256) ? 1 : 256 / T;
+    static constexpr int CAP0 = 32768 / (NX * (int)sizeof(cplx<R>));
+    static constexpr int CAP = CAP0 < 1 ? 1 : CAP0;
+    static constexpr int ROWS = ROWS0 < CAP ? ROWS0 : CAP;
+    static constexpr int THREADS = T * ROWS;
+};
+
+// ---------------------------------------------------------------- rows_fwd
+// grid: ceil(C * N / n0 / ROWS); block: THREADS.  w[row] = FFT_x(B x + y) (FWD_BORN)
+// or FFT_x(x) (FWD_COPY).
+template <typename R, int NX, int RX>
+__global__ void __launch_bounds__(RowCfg<R, NX, RX>::THREADS)
+k_rows_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y,
+           cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int mode, int adj)
+{
+    using CT = cplx<R>;
+    using Cfg = RowCfg<R, NX, RX>;
+    constexpr int T = Cfg::T;
+    __shared__ CT sm[Cfg::ROWS * NX];
+    const int lr = threadIdx.x / T, t = threadIdx.x % T;
+    const long long rows_per_comp = d.N / NX;
+    const long long C = d.D + 1;
+    long long row = (long long)blockIdx.x * Cfg::ROWS + lr;
+    const bool valid = row < C * rows_per_comp;
+    if (!valid) row = 0;
+    const int c = (int)(row / rows_per_comp);
+    const long long rest = row % rows_per_comp;
+    const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
+    const long long vbase = rest * NX;
+    const long long fbase = (long long)c * d.N + vbase;
+    const RowB<R> rb = row_B(M, d.D, c, i1, i2, vbase);
+    CT v[RX];
+#pragma unroll
+    for (int s = 0; s < RX; ++s) {
+        const int i0 = t + T * slot_q<NX, RX, 0>(s);
+        CT xv = x[fbase + i0];
+        if (mode == FWD_BORN) {
+            const CT b = born_B(M, rb, i0, adj != 0);
+            v[s] = cadd(cmul(b, xv), y[fbase + i0]);
+        } else {
+            v[s] = xv;
+        }
+    }
+    fft_run<NX, RX, -1>(v, sm + lr * NX, 1, t, tw, RowSync<T>());
+    if (valid) {
+        constexpr int np = plan_npass(NX, RX);
+#pragma unroll
+        for (int s = 0; s < RX; ++s) w[fbase + t + T * slot_q<NX, RX, np>(s)] = v[s];
+    }
+}
+
+// ---------------------------------------------------------------- rows_inv
+// INV_BORN:  z = IFFT_x(w);  dx = nu B (z - x);  x += dx;  partial (|dx|^2, |x|^2)
+// INV_RESID: z = IFFT_x(w) = L x;  r = y - z - v x;  w <- r;  partial (|r|^2, |y|^2)
+// INV_APPLY: z = IFFT_x(w) = L x;  w <- z + v x;           partial (|w|^2, 0)
+// INV_PLAIN: w <- IFFT_x(w);                               partial (|w|^2, 0)
+template <typename R, int NX, int RX>
+__global__ void __launch_bounds__(RowCfg<R, NX, RX>::THREADS)
+k_rows_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y, cplx<R>* __restrict__ w,
+           const cplx<R>* __restrict__ tw, int mode, int adj, R nu, double* __restrict__ partials)
+{
+    using CT = cplx<R>;
+    using Cfg = RowCfg<R, NX, RX>;
+    constexpr int T = Cfg::T;
+    constexpr int np = plan_npass(NX, RX);
+    __shared__ CT sm[Cfg::ROWS * NX];
+    const int lr = threadIdx.x / T, t = threadIdx.x % T;
+    const long long rows_per_comp = d.N / NX;
+    const long long C = d.D + 1;
+    long long row = (long long)blockIdx.x * Cfg::ROWS + lr;
+    const bool valid = row < C * rows_per_comp;
+    if (!valid) row = 0;
+    const int c = (int)(row / rows_per_comp);
+    const long long rest = row % rows_per_comp;
+    const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
+    const long long vbase = rest * NX;
+    const long long fbase = (long long)c * d.N + vbase;
+    const RowB<R> rb = row_B(M, d.D, c, i1, i2, vbase);
+    CT v[RX];
+#pragma unroll
+    for (int s = 0; s < RX; ++s) v[s] = w[fbase + t + T * slot_q<NX, RX, 0>(s)];
+    fft_run<NX, RX, +1>(v, sm + lr * NX, 1, t, tw, RowSync<T>());
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int s = 0; s < RX; ++s) {
+        const int i0 = t + T * slot_q<NX, RX, np>(s);
+        const long long f = fbase + i0;
+        if (mode == INV_PLAIN) {
+            if (valid) w[f] = v[s];
+            s0 += (double)cabs2(v[s]);
+            continue;
+        }
+        const CT xv = x[f];
+        const CT b = born_B(M, rb, i0, adj != 0);
+        if (mode == INV_BORN) {
+            const CT del = cscale(cmul(b, csub(v[s], xv)), nu);
+            const CT xn = cadd(xv, del);
+            if (valid) x[f] = xn;
+            s0 += (double)cabs2(del);
+            s1 += (double)cabs2(xn);
+        } else {
+            // v x = (1 - B) x
+            const CT vx = csub(xv, cmul(b, xv));
+            if (mode == INV_RESID) {
+                const CT yv = y[f];
+                const CT r = csub(yv, cadd(v[s], vx));
+                if (valid) w[f] = r;
+                s0 += (double)cabs2(r);
+                s1 += (double)cabs2(yv);
+            } else {
+                const CT a = cadd(v[s], vx);
+                if (valid) w[f] = a;
+                s0 += (double)cabs2(a);
+            }
+        }
+    }
+    if (!valid) { s0 = 0.0; s1 = 0.0; }
+    block_sum2(s0, s1, partials + 2 * (long long)blockIdx.x);
+}
+
+// ---------------------------------------------------------------- axis_fft
+// FFT along axis 1 (y) of a 3D field, in place, COLS x-columns per block.
+// grid: C * n2 * ceil(n0 / COLS); block: (NA/RA) * COLS.
+template <int NA, int RA, int COLS> struct AxisCfg {
+    static constexpr int T = NA / RA;
+    static constexpr int THREADS = T * COLS;
+};
+
+template <typename R, int NA, int RA, int COLS, int S>
+__global__ void __launch_bounds__(AxisCfg<NA, RA, COLS>::THREADS)
+k_axis_fft(Dims d, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw)
+{
+    using CT = cplx<R>;
+    constexpr int T = NA / RA;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CT* sm = reinterpret_cast<CT*>(smraw);
+    const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    const int xblocks = (d.n0 + COLS - 1) / COLS;
+    const int xb = blockIdx.x % xblocks;
+    const long long rest = blockIdx.x / xblocks;  // c * n2 + i2
+    const int i0 = xb * COLS + col;
+    const bool valid = i0 < d.n0;
+    const long long base = rest * (long long)d.n0 * d.n1 + (valid ? i0 : 0);
+    CT v[RA];
+#pragma unroll
+    for (int s = 0; s < RA; ++s) v[s] = w[base + (long long)(t + T * slot_q<NA, RA, 0>(s)) * d.n0];
+    fft_run<NA, RA, S>(v, sm + col, COLS, t, tw, BlockSync());
+    if (valid) {
+        constexpr int np = plan_npass(NA, RA);
+#pragma unroll
+        for (int s = 0; s < RA; ++s) w[base + (long long)(t + T * slot_q<NA, RA, np>(s)) * d.n0] = v[s];
+    }
+}
+
+// ------------------------------------------------------------- last_symbol
+// Forward FFT along the last axis, per-wavenumber symbol on all C components,
+// inverse FFT along the last axis.  grid: (D == 3 ? n1 : 1) * ceil(n0 / COLS).
+template <typename R, int C>
+__device__ __forceinline__ void apply_symbol(const Symbol<R>& Sy, int mode, const cplx<R>* t, R k2, cplx<R>* v)
+{
+    using CT = cplx<R>;
+    constexpr int D = C - 1;
+    if (mode == SYM_GREEN || mode == SYM_GREEN_ADJ) {
+        const bool adj = mode == SYM_GREEN_ADJ;
+        const CT P = adj ? cconj(Sy.P) : Sy.P;
+        const CT Pu = adj ? cconj(Sy.Pu) : Sy.Pu;
+        const CT c1 = adj ? cconj(Sy.c1) : Sy.c1;
+        const CT c2 = adj ? cconj(Sy.c2) : Sy.c2;
+        const CT c3 = adj ? cconj(Sy.c3) : Sy.c3;
+        // mu = k^2 + (a1 + l1)(a2 + l2);  im = scale / mu
+        const CT mu = mk<CT, R>(k2 + c3.x, c3.y);
+        const R inv = Sy.scale / cabs2(mu);
+        const CT im = mk<CT, R>(mu.x * inv, -mu.y * inv);
+        CT s = mk<CT, R>((R)0, (R)0);
+#pragma unroll
+        for (int e = 0; e < D; ++e) s = cadd(s, cmulc(v[e], t[e]));  // sum conj(t_e) v_e
+        const CT vp = v[D];
+        const CT tmp = cmul(cadd(cmul(Pu, s), cmul(c1, vp)), im);
+#pragma unroll
+        for (int e = 0; e < D; ++e) v[e] = csub(cmul(P, v[e]), cmul(t[e], tmp));
+        v[D] = cmul(csub(cmul(c2, vp), cmul(c1, s)), im);
+    } else {
+        const bool adj = mode == SYM_L_ADJ;
+        const CT la1 = adj ? cconj(Sy.la1) : Sy.la1;
+        const CT la2 = adj ? cconj(Sy.la2) : Sy.la2;
+        const R g = adj ? -Sy.isq * Sy.scale : Sy.isq * Sy.scale;  // off-diagonal i -> -i for L^H
+        const CT vp = v[D];
+        CT sp = cmul(la2, vp);
+        sp = cscale(sp, Sy.scale);
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            const CT ve = v[e];
+            // i t_e g v_p  and  i conj(t_e) g v_e
+            v[e] = cadd(cscale(cmul(la1, ve), Sy.scale), cscale(mul_si<1>(cmul(t[e], vp)), g));
+            sp = cadd(sp, cscale(mul_si<1>(cmulc(ve, t[e])), g));
+        }
+        v[D] = sp;
+    }
+}
+
+template <typename R, int NL, int RL, int COLS, int C>
+__global__ void __launch_bounds__((NL / RL) * COLS)
+k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int mode)
+{
+    using CT = cplx<R>;
+    constexpr int T = NL / RL;
+    constexpr int D = C - 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CT* sm = reinterpret_cast<CT*>(smraw);
+    const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    const int xblocks = (d.n0 + COLS - 1) / COLS;
+    const int xb = blockIdx.x % xblocks;
+    const int i1 = (D == 3) ? (int)(blockIdx.x / xblocks) : 0;
+    const int i0 = xb * COLS + col;
+    const bool valid = i0 < d.n0;
+    const long long astride = (D == 3) ? (long long)d.n0 * d.n1 : (long long)d.n0;
+    const long long base = (D == 3 ? (long long)i1 * d.n0 : 0) + (valid ? i0 : 0);
+    CT v[C][RL];
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int s = 0; s < RL; ++s)
+            v[c][s] = w[(long long)c * d.N + base + (long long)(t + T * slot_q<NL, RL, 0>(s)) * astride];
+    const int cstride = NL * COLS;
+    fft_run_multi<NL, RL, C, -1>(v, sm + col, COLS, cstride, t, tw, BlockSync());
+    // per-wavenumber symbol
+    constexpr int np = plan_npass(NL, RL);
+    const int ic0 = valid ? i0 : 0;
+    CT tx[D];
+    R k2c = Sy.k2[0][ic0];
+    tx[0] = Sy.kt[0][ic0];
+    if (D == 3) {
+        tx[1] = Sy.kt[1][i1];
+        k2c += Sy.k2[1][i1];
+    }
+#pragma unroll
+    for (int s = 0; s < RL; ++s) {
+        const int il = t + T * slot_q<NL, RL, np>(s);
+        tx[D - 1] = Sy.kt[D - 1][il];
+        const R k2 = k2c + Sy.k2[D - 1][il];
+        CT vv[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) vv[c] = v[c][s];
+        apply_symbol<R, C>(Sy, mode, tx, k2, vv);
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c][s] = vv[c];
+    }
+    // the thread owns the same positions after the forward transform; reorder
+    // its registers into the entry order of the inverse transform
+#pragma unroll
+    for (int c = 0; c < C; ++c) permute_slots<NL, RL, np, 0>(v[c]);
+    fft_run_multi<NL, RL, C, +1>(v, sm + col, COLS, cstride, t, tw, BlockSync());
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int s = 0; s < RL; ++s)
+                w[(long long)c * d.N + base + (long long)(t + T * slot_q<NL, RL, np>(s)) * astride] = v[c][s];
+    }
+}
+
+}  // namespace cbs

@@ -1,0 +1,1240 @@
+// cbs_api.cu -- C ABI of the Born solver: set-up (Algorithm 1 preprocessing),
+// the FP64 / FP32 / FP32+FP64-refinement drivers, the adjoint, and the
+// operator entry points used for step-by-step checks.  All compute runs in
+// the kernels of born.cuh and the set-up/utility kernels below; the host
+// only computes O(n) per-axis tables and scalars.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cbs.h"
+#include "launch.cuh"
+
+namespace cbs {
+CBS_EXTERN_LAUNCHERS(float)
+CBS_EXTERN_LAUNCHERS(double)
+}  // namespace cbs
+
+using namespace cbs;
+
+namespace {
+
+constexpr int kHistCap = 8192;
+constexpr int kSetupThreads = 256;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+thread_local std::string g_create_error = "no error";
+
+// ---------------------------------------------------------------- set-up kernels
+struct SetupIn {
+    int D, n0, n1, n2;
+    long long N;
+    double omega;
+    const double* c0;
+    const double* rho;
+    const double* alpha;
+    const double* gc[3];
+    const double* gs[3];
+};
+
+__device__ __forceinline__ void unravel(const SetupIn& s, long long i, int& i0, int& i1, int& i2)
+{
+    i0 = (int)(i % s.n0);
+    long long r = i / s.n0;
+    i1 = (int)(r % s.n1);
+    i2 = (int)(r / s.n1);
+}
+
+__device__ __forceinline__ long long plus_one(const SetupIn& s, int eta, int i0, int i1, int i2)
+{
+    if (eta == 0) i0 = (i0 + 1) % s.n0;
+    else if (eta == 1) i1 = (i1 + 1) % s.n1;
+    else i2 = (i2 + 1) % s.n2;
+    return ((long long)i2 * s.n1 + i1) * s.n0 + i0;
+}
+
+__device__ __forceinline__ double gamma_c(const SetupIn& s, int i0, int i1, int i2)
+{
+    double g = s.gc[0][i0] + s.gc[1][i1];
+    if (s.D == 3) g += s.gc[2][i2];
+    return g;
+}
+
+__device__ __forceinline__ double gamma_s(const SetupIn& s, int eta, int i0, int i1, int i2)
+{
+    double g = (eta == 0 ? s.gs[0][i0] : s.gc[0][i0]) + (eta == 1 ? s.gs[1][i1] : s.gc[1][i1]);
+    if (s.D == 3) g += (eta == 2 ? s.gs[2][i2] : s.gc[2][i2]);
+    return g;
+}
+
+// diagonal values of the row-scaled system (eq. HH1stOrderSH, App. B.1):
+//   d_eta = (S+ rho)_eta (S+ gamma_eta + i omega),  q = (i omega + gamma) / (rho c^2)
+// with 1 / (rho c^2) = (1 - i 2 alpha c0 / omega) / (rho c0^2)   (eq. 118)
+__device__ __forceinline__ void diag_values(const SetupIn& s, long long i, double2* d, double2& q)
+{
+    int i0, i1, i2;
+    unravel(s, i, i0, i1, i2);
+    const double rho = s.rho[i], c0 = s.c0[i], al = s.alpha[i];
+    const double kap = 1.0 / (rho * c0 * c0), et = 2.0 * al * c0 / s.omega;
+    const double g = gamma_c(s, i0, i1, i2);
+    q = make_double2(kap * (g + et * s.omega), kap * (s.omega - g * et));
+    for (int eta = 0; eta < s.D; ++eta) {
+        const double rs = 0.5 * (rho + s.rho[plus_one(s, eta, i0, i1, i2)]);
+        d[eta] = make_double2(rs * gamma_s(s, eta, i0, i1, i2), rs * s.omega);
+    }
+}
+
+// per block: min/max of Re, Im over d (all eta) and q; invalid-input flag
+__global__ void k_setup_minmax(SetupIn s, double* part, int* bad)
+{
+    double v[8] = {INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.N; i += (long long)gridDim.x * blockDim.x) {
+        const double c0 = s.c0[i], rho = s.rho[i], al = s.alpha[i];
+        if (!(isfinite(c0) && isfinite(rho) && isfinite(al)) || !(c0 > 0.0) || !(rho > 0.0) || !(al >= 0.0)) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        double2 d[3], q;
+        diag_values(s, i, d, q);
+        for (int e = 0; e < s.D; ++e) {
+            v[0] = fmin(v[0], d[e].x); v[1] = fmax(v[1], d[e].x);
+            v[2] = fmin(v[2], d[e].y); v[3] = fmax(v[3], d[e].y);
+        }
+        v[4] = fmin(v[4], q.x); v[5] = fmax(v[5], q.x);
+        v[6] = fmin(v[6], q.y); v[7] = fmax(v[7], q.y);
+    }
+    __shared__ double sh[8][kSetupThreads];
+    for (int k = 0; k < 8; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int k = 0; k < 8; ++k)
+                sh[k][threadIdx.x] = (k & 1) ? fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + o])
+                                             : fmin(sh[k][threadIdx.x], sh[k][threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) part[blockIdx.x * 8 + k] = sh[k][0];
+}
+
+// per block: max |d - a1|, max |q - a2|
+__global__ void k_setup_maxdev(SetupIn s, double2 a1, double2 a2, double* part)
+{
+    double m1 = 0.0, m2 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.N; i += (long long)gridDim.x * blockDim.x) {
+        double2 d[3], q;
+        diag_values(s, i, d, q);
+        for (int e = 0; e < s.D; ++e) m1 = fmax(m1, hypot(d[e].x - a1.x, d[e].y - a1.y));
+        m2 = fmax(m2, hypot(q.x - a2.x, q.y - a2.y));
+    }
+    __shared__ double sh[2][kSetupThreads];
+    sh[0][threadIdx.x] = m1;
+    sh[1][threadIdx.x] = m2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + o]);
+            sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part[blockIdx.x * 2] = sh[0][0]; part[blockIdx.x * 2 + 1] = sh[1][0]; }
+}
+
+// all diagonal values (for the median shift rule): dv[eta*N + i], qv[i]
+__global__ void k_setup_values(SetupIn s, double2* dv, double2* qv)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.N; i += (long long)gridDim.x * blockDim.x) {
+        double2 d[3], q;
+        diag_values(s, i, d, q);
+        for (int e = 0; e < s.D; ++e) dv[e * s.N + i] = d[e];
+        qv[i] = q;
+    }
+}
+
+// per-voxel arrays the iteration kernels read: rs_eta = (S+ rho)_eta / lambda1,
+// kp = 1 / (rho c0^2 lambda2), et = 2 alpha c0 / omega  (float64 and float32)
+__global__ void k_setup_store(SetupIn s, double il1, double il2, double* rs64_0, double* rs64_1, double* rs64_2,
+                              double* kp64, double* et64, float* rs32_0, float* rs32_1, float* rs32_2, float* kp32,
+                              float* et32)
+{
+    double* rs64[3] = {rs64_0, rs64_1, rs64_2};
+    float* rs32[3] = {rs32_0, rs32_1, rs32_2};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.N; i += (long long)gridDim.x * blockDim.x) {
+        int i0, i1, i2;
+        unravel(s, i, i0, i1, i2);
+        const double rho = s.rho[i], c0 = s.c0[i];
+        for (int e = 0; e < s.D; ++e) {
+            const double r = 0.5 * (rho + s.rho[plus_one(s, e, i0, i1, i2)]) * il1;
+            rs64[e][i] = r;
+            rs32[e][i] = (float)r;
+        }
+        const double kp = 1.0 / (rho * c0 * c0) * il2;
+        const double et = 2.0 * s.alpha[i] * c0 / s.omega;
+        kp64[i] = kp;
+        et64[i] = et;
+        kp32[i] = (float)kp;
+        et32[i] = (float)et;
+    }
+}
+
+// ---------------------------------------------------------------- field kernels
+struct ScaleIn {
+    int D;
+    long long N;
+    const double* rs[3];
+    const double* kp;
+    const double* et;
+    double sl1, sl2;  // sqrt(lambda1), sqrt(lambda2)
+};
+
+// y = C^-1/2 s_hat,  s_hat_u = (S+ rho) s_u,  s_hat_p = s_p / (rho c^2)
+// (rs sqrt(l1) = (S+ rho)/sqrt(l1);  kp sqrt(l2) (1 - i et) = 1/(rho c^2 sqrt(l2)))
+__global__ void k_scale_source(ScaleIn p, const double2* __restrict__ src, double2* __restrict__ y, int adjoint)
+{
+    const long long total = (long long)(p.D + 1) * p.N;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(j / p.N);
+        const long long i = j - (long long)c * p.N;
+        const double2 v = src[j];
+        if (adjoint) {
+            const double f = 1.0 / (c < p.D ? p.sl1 : p.sl2);
+            y[j] = make_double2(v.x * f, v.y * f);
+        } else if (c < p.D) {
+            const double f = p.rs[c][i] * p.sl1;
+            y[j] = make_double2(v.x * f, v.y * f);
+        } else {
+            const double k = p.kp[i] * p.sl2, e = p.et[i];
+            // v * k (1 - i e)
+            y[j] = make_double2(k * (v.x + e * v.y), k * (v.y - e * v.x));
+        }
+    }
+}
+
+// out = C^{mode} in with mode -1/2 (unscale) or +1/2 (physical -> scaled)
+__global__ void k_scale_blocks(int D, long long N, double f1, double f2, const double2* __restrict__ in,
+                               double2* __restrict__ out)
+{
+    const long long total = (long long)(D + 1) * N;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+        const double f = (j < (long long)D * N) ? f1 : f2;
+        const double2 v = in[j];
+        out[j] = make_double2(v.x * f, v.y * f);
+    }
+}
+
+__global__ void k_cast_64_32(const double2* __restrict__ a, float2* __restrict__ b, double s, long long n)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const double2 v = a[j];
+        b[j] = make_float2((float)(v.x * s), (float)(v.y * s));
+    }
+}
+
+__global__ void k_cast_32_64(const float2* __restrict__ a, double2* __restrict__ b, long long n)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const float2 v = a[j];
+        b[j] = make_double2((double)v.x, (double)v.y);
+    }
+}
+
+// x64 += s * x32   (refinement correction accumulated in float64)
+__global__ void k_axpy_32_64(double2* __restrict__ x, const float2* __restrict__ d, double s, long long n)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const float2 v = d[j];
+        double2 a = x[j];
+        a.x = fma(s, (double)v.x, a.x);
+        a.y = fma(s, (double)v.y, a.y);
+        x[j] = a;
+    }
+}
+
+// per-block partial sums of |a|^2 (grid-stride, fixed assignment -> deterministic)
+__global__ void k_norm2(const double2* __restrict__ a, long long n, double* part)
+{
+    double s = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const double2 v = a[j];
+        s += v.x * v.x + v.y * v.y;
+    }
+    block_sum2(s, 0.0, part + 2 * blockIdx.x);
+}
+
+// Fixed-order sum of nblk partial pairs -> out[0..1]; optionally appends
+// (out0, out1) to the history ring at *counter.
+__global__ void k_reduce(const double* __restrict__ part, int nblk, double* out, double* hist, int* counter, int cap)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    block_sum2(a, b, out);
+    if (hist != nullptr && threadIdx.x == 0) {
+        __threadfence_block();
+        const int k = *counter;
+        hist[2 * (k % cap)] = out[0];
+        hist[2 * (k % cap) + 1] = out[1];
+        *counter = k + 1;
+    }
+}
+
+inline int grid_for(long long n, int threads = 256)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+// ====================================================================== solver
+struct cbs_solver {
+    int D = 0, C = 0;
+    int n[3] = {1, 1, 1};
+    long long N = 0;
+    double dx = 0, omega = 0;
+    cbs_options opt{};
+    cbs_boundary bnd{};
+    double a1r = 0, a1i = 0, a2r = 0, a2i = 0, lam1 = 0, lam2 = 0;
+    double t_setup_ms = 0;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev_user = nullptr, ev0 = nullptr, ev1 = nullptr;
+    std::string err = "no error";
+    std::vector<void*> allocs;
+
+    double *rs64[3] = {}, *kp64 = nullptr, *et64 = nullptr;
+    float *rs32[3] = {}, *kp32 = nullptr, *et32 = nullptr;
+    double *gc64[3] = {}, *gs64[3] = {};
+    float *gc32[3] = {}, *gs32[3] = {};
+    double2* kt64[3] = {};
+    double* k264[3] = {};
+    float2* kt32[3] = {};
+    float* k232[3] = {};
+    double2* tw64[3] = {};
+    float2* tw32[3] = {};
+
+    double2 *x64 = nullptr, *y64 = nullptr, *w64 = nullptr;
+    float2 *x32 = nullptr, *y32 = nullptr, *w32 = nullptr;
+    double* partials = nullptr;
+    int npart = 0;
+    double* red = nullptr;      // [2] result of the last reduction
+    double* hist = nullptr;     // [kHistCap][2]
+    int* counter = nullptr;
+    double* host_red = nullptr; // pinned [2 * kHistCap]
+
+    Plan<double> P64{};
+    Plan<float> P32{};
+    cudaGraphExec_t graph64[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph32[2] = {nullptr, nullptr};
+    int graphK64[2] = {0, 0}, graphK32[2] = {0, 0};
+    bool warmed64 = false, warmed32 = false;
+    int hist_pos = 0;  // host mirror of *counter
+    long long launches = 0;  // kernels launched by the current call
+};
+
+namespace {
+
+struct Fail {
+    cbs_status code;
+};
+
+#define CUDA_TRY(expr)                                                                                                \
+    do {                                                                                                              \
+        cudaError_t e_ = (expr);                                                                                      \
+        if (e_ != cudaSuccess) {                                                                                      \
+            throw CudaError{e_, #expr, __LINE__};                                                                     \
+        }                                                                                                             \
+    } while (0)
+
+struct CudaError {
+    cudaError_t e;
+    const char* what;
+    int line;
+};
+
+template <typename T> T* dalloc(cbs_solver* s, size_t count)
+{
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{CBS_ENOMEM};
+    }
+    s->allocs.push_back(p);
+    return static_cast<T*>(p);
+}
+
+cbs_status set_err(cbs_solver* s, cbs_status code, const std::string& msg)
+{
+    if (s) s->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+// ---------------------------------------------------------------- host tables
+double layer_depth(double xi, long n, int lo, int hi)
+{
+    double d = 0.0;
+    if (lo > 0) d = std::max(d, (lo - xi) / lo);
+    if (hi > 0) d = std::max(d, (xi - (double)(n - 1 - hi)) / hi);
+    return std::min(1.0, d);
+}
+
+double layer_gamma(double xi, long n, int lo, int hi, double gmax, double power)
+{
+    const double d = layer_depth(xi, n, lo, hi);
+    return d > 0.0 ? gmax * std::pow(d, power) : 0.0;
+}
+
+template <typename T> void upload(cbs_solver* s, T* dst, const std::vector<T>& v)
+{
+    CUDA_TRY(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s->st));
+}
+
+// ---------------------------------------------------------------- iteration pieces
+template <typename R> struct Bufs;
+template <> struct Bufs<double> {
+    static Plan<double>& plan(cbs_solver* s) { return s->P64; }
+    static double2* x(cbs_solver* s) { return s->x64; }
+    static double2* y(cbs_solver* s) { return s->y64; }
+    static double2* w(cbs_solver* s) { return s->w64; }
+    static cudaGraphExec_t* graph(cbs_solver* s) { return s->graph64; }
+    static int* graphK(cbs_solver* s) { return s->graphK64; }
+    static bool& warmed(cbs_solver* s) { return s->warmed64; }
+};
+template <> struct Bufs<float> {
+    static Plan<float>& plan(cbs_solver* s) { return s->P32; }
+    static float2* x(cbs_solver* s) { return s->x32; }
+    static float2* y(cbs_solver* s) { return s->y32; }
+    static float2* w(cbs_solver* s) { return s->w32; }
+    static cudaGraphExec_t* graph(cbs_solver* s) { return s->graph32; }
+    static int* graphK(cbs_solver* s) { return s->graphK32; }
+    static bool& warmed(cbs_solver* s) { return s->warmed32; }
+};
+
+template <typename R> void reduce(cbs_solver* s, int nblk, bool record)
+{
+    k_reduce<<<1, 256, 0, s->st>>>(s->partials, nblk, s->red, record ? s->hist : nullptr, s->counter, kHistCap);
+    CUDA_TRY(cudaGetLastError());
+    if (record) s->hist_pos++;
+}
+
+// one Born iteration on the precision-R buffers (eq. BornAlt)
+template <typename R> void iterate_once(cbs_solver* s, bool adj)
+{
+    Plan<R>& P = Bufs<R>::plan(s);
+    auto x = Bufs<R>::x(s);
+    auto y = Bufs<R>::y(s);
+    auto w = Bufs<R>::w(s);
+    CUDA_TRY(launch_rows_fwd<R>(P, x, y, w, FWD_BORN, adj, s->st));
+    if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, -1, s->st));
+    CUDA_TRY(launch_last<R>(P, w, adj ? SYM_GREEN_ADJ : SYM_GREEN, s->st));
+    if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, +1, s->st));
+    CUDA_TRY(launch_rows_inv<R>(P, x, y, w, INV_BORN, adj, (R)s->opt.nu, s->partials, s->st));
+    reduce<R>(s, rows_blocks<R>(P), true);
+    s->launches += (s->D == 3) ? 6 : 4;
+}
+
+// run n iterations, K at a time through a captured CUDA graph
+template <typename R> void run_iterations(cbs_solver* s, int n, bool adj)
+{
+    const int K = s->opt.check_every;
+    bool& warmed = Bufs<R>::warmed(s);
+    while (n > 0) {
+        if (!warmed || n < K) {
+            iterate_once<R>(s, adj);
+            warmed = true;
+            --n;
+            continue;
+        }
+        cudaGraphExec_t& ge = Bufs<R>::graph(s)[adj ? 1 : 0];
+        int& gk = Bufs<R>::graphK(s)[adj ? 1 : 0];
+        if (ge == nullptr || gk != K) {
+            if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+            const int pos0 = s->hist_pos;
+            try {
+                for (int k = 0; k < K; ++k) iterate_once<R>(s, adj);
+            } catch (...) {
+                cudaStreamEndCapture(s->st, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            s->hist_pos = pos0;
+            s->launches -= (long long)K * ((s->D == 3) ? 6 : 4);
+            CUDA_TRY(cudaStreamEndCapture(s->st, &g));
+            cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            CUDA_TRY(e);
+            gk = K;
+        }
+        CUDA_TRY(cudaGraphLaunch(ge, s->st));
+        s->hist_pos += K;
+        s->launches += (long long)K * ((s->D == 3) ? 6 : 4);
+        n -= K;
+    }
+}
+
+// w <- y - A_s x (mode INV_RESID) or w <- A_s x (INV_APPLY); red = (|w|^2, |y|^2)
+template <typename R> void apply_operator(cbs_solver* s, bool adj, int mode)
+{
+    Plan<R>& P = Bufs<R>::plan(s);
+    auto x = Bufs<R>::x(s);
+    auto y = Bufs<R>::y(s);
+    auto w = Bufs<R>::w(s);
+    CUDA_TRY(launch_rows_fwd<R>(P, x, y, w, FWD_COPY, adj, s->st));
+    if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, -1, s->st));
+    CUDA_TRY(launch_last<R>(P, w, adj ? SYM_L_ADJ : SYM_L, s->st));
+    if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, +1, s->st));
+    CUDA_TRY(launch_rows_inv<R>(P, x, y, w, mode, adj, (R)0, s->partials, s->st));
+    reduce<R>(s, rows_blocks<R>(P), false);
+    s->launches += (s->D == 3) ? 6 : 4;
+}
+
+// w <- (L+I)^-1 x (or its adjoint)
+template <typename R> void apply_green(cbs_solver* s, bool adj)
+{
+    Plan<R>& P = Bufs<R>::plan(s);
+    auto x = Bufs<R>::x(s);
+    auto y = Bufs<R>::y(s);
+    auto w = Bufs<R>::w(s);
+    CUDA_TRY(launch_rows_fwd<R>(P, x, y, w, FWD_COPY, adj, s->st));
+    if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, -1, s->st));
+    CUDA_TRY(launch_last<R>(P, w, adj ? SYM_GREEN_ADJ : SYM_GREEN, s->st));
+    if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, +1, s->st));
+    CUDA_TRY(launch_rows_inv<R>(P, x, y, w, INV_PLAIN, adj, (R)0, s->partials, s->st));
+    s->launches += (s->D == 3) ? 5 : 3;
+}
+
+void read_red(cbs_solver* s, double* out2)
+{
+    CUDA_TRY(cudaMemcpyAsync(s->host_red, s->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CUDA_TRY(cudaStreamSynchronize(s->st));
+    out2[0] = s->host_red[0];
+    out2[1] = s->host_red[1];
+}
+
+// last history entry (|dx|^2, |x|^2) -> relative increment
+double read_last_increment(cbs_solver* s)
+{
+    const int k = (s->hist_pos - 1) % kHistCap;
+    CUDA_TRY(cudaMemcpyAsync(s->host_red, s->hist + 2 * k, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CUDA_TRY(cudaStreamSynchronize(s->st));
+    return s->host_red[1] > 0 ? std::sqrt(s->host_red[0] / s->host_red[1]) : 0.0;
+}
+
+void norm2_64(cbs_solver* s, const double2* a, long long n, double* out)
+{
+    const int g = std::min(grid_for(n), s->npart);
+    k_norm2<<<g, 256, 0, s->st>>>(a, n, s->partials);
+    CUDA_TRY(cudaGetLastError());
+    k_reduce<<<1, 256, 0, s->st>>>(s->partials, g, s->red, nullptr, nullptr, kHistCap);
+    CUDA_TRY(cudaGetLastError());
+    s->launches += 2;
+    double r[2];
+    read_red(s, r);
+    *out = r[0];
+}
+
+void begin_call(cbs_solver* s)
+{
+    cudaStream_t us = (cudaStream_t)s->opt.stream;
+    CUDA_TRY(cudaEventRecord(s->ev_user, us));
+    CUDA_TRY(cudaStreamWaitEvent(s->st, s->ev_user, 0));
+}
+
+ScaleIn scale_in(cbs_solver* s)
+{
+    ScaleIn p;
+    p.D = s->D;
+    p.N = s->N;
+    for (int e = 0; e < 3; ++e) p.rs[e] = s->rs64[e];
+    p.kp = s->kp64;
+    p.et = s->et64;
+    p.sl1 = std::sqrt(s->lam1);
+    p.sl2 = std::sqrt(s->lam2);
+    return p;
+}
+
+long long field_len(cbs_solver* s) { return (long long)s->C * s->N; }
+
+// physical source -> y64 ; optional start field -> x64 (C^1/2 (u,p)) else 0
+void prepare(cbs_solver* s, const void* src, const void* x0, bool adj)
+{
+    const long long n = field_len(s);
+    k_scale_source<<<grid_for(n), 256, 0, s->st>>>(scale_in(s), (const double2*)src, s->y64, adj ? 1 : 0);
+    CUDA_TRY(cudaGetLastError());
+    s->launches += x0 ? 2 : 1;
+    if (x0) {
+        k_scale_blocks<<<grid_for(n), 256, 0, s->st>>>(s->D, s->N, std::sqrt(s->lam1), std::sqrt(s->lam2),
+                                                       (const double2*)x0, s->x64);
+        CUDA_TRY(cudaGetLastError());
+    } else {
+        CUDA_TRY(cudaMemsetAsync(s->x64, 0, n * sizeof(double2), s->st));
+    }
+}
+
+void finish_field(cbs_solver* s, void* field)
+{
+    const long long n = field_len(s);
+    k_scale_blocks<<<grid_for(n), 256, 0, s->st>>>(s->D, s->N, 1.0 / std::sqrt(s->lam1), 1.0 / std::sqrt(s->lam2),
+                                                   s->x64, (double2*)field);
+    CUDA_TRY(cudaGetLastError());
+    s->launches += 1;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+// plain FP64 (or plain FP32) solve on the scaled variables; x64/y64 prepared
+template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* info)
+{
+    const long long n = field_len(s);
+    double ny2;
+    norm2_64(s, s->y64, n, &ny2);
+    if (!(ny2 > 0)) {  // zero source: zero field
+        CUDA_TRY(cudaMemsetAsync(s->x64, 0, n * sizeof(double2), s->st));
+        info->rel_residual = 0;
+        return CBS_OK;
+    }
+    if (std::is_same<R, float>::value) {
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->y64, s->y32, 1.0, n);
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->x64, s->x32, 1.0, n);
+        CUDA_TRY(cudaGetLastError());
+        s->launches += 2;
+    }
+    const double tol = s->opt.tol;
+    const int maxit = s->opt.max_iter;
+    int it = 0;
+    double rel = 1.0, inc = 0.0;
+    cbs_status st = CBS_OK;
+    while (it < maxit) {
+        const int blk = std::min(s->opt.check_every, maxit - it);
+        run_iterations<R>(s, blk, adj);
+        it += blk;
+        inc = read_last_increment(s);
+        if (tol > 0) {
+            apply_operator<R>(s, adj, INV_RESID);
+            double r[2];
+            read_red(s, r);
+            info->residual_checks++;
+            rel = std::sqrt(r[0] / r[1]);
+            if (!finite(rel) || !finite(inc)) { st = CBS_EDIVERGED; break; }
+            if (rel <= tol) break;
+        } else if (!finite(inc)) {
+            st = CBS_EDIVERGED;
+            break;
+        }
+    }
+    if (st == CBS_OK && tol > 0 && rel > tol) st = CBS_ENOCONV;
+    if (std::is_same<R, float>::value) {
+        k_cast_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x32, s->x64, n);
+        CUDA_TRY(cudaGetLastError());
+        s->launches += 1;
+    }
+    info->iters = it;
+    info->rel_residual = tol > 0 ? rel : -1.0;
+    info->rel_increment = inc;
+    return st;
+}
+
+// FP32 inner Born iterations with FP64 residual, norm and correction
+cbs_status solve_refine(cbs_solver* s, bool adj, cbs_info* info)
+{
+    const long long n = field_len(s);
+    double ny2;
+    norm2_64(s, s->y64, n, &ny2);
+    if (!(ny2 > 0)) {
+        CUDA_TRY(cudaMemsetAsync(s->x64, 0, n * sizeof(double2), s->st));
+        info->rel_residual = 0;
+        return CBS_OK;
+    }
+    const double tol = s->opt.tol > 0 ? s->opt.tol : 1e-6;
+    const int maxit = s->opt.max_iter;
+    // r = y - A_s x in float64 (into w64)
+    double r[2];
+    apply_operator<double>(s, adj, INV_RESID);
+    read_red(s, r);
+    info->residual_checks++;
+    double rn2 = r[0];
+    double rel = std::sqrt(rn2 / ny2), inc = 0.0;
+    int it = 0, outer = 0;
+    cbs_status st = CBS_OK;
+    while (rel > tol && it < maxit) {
+        const double rn = std::sqrt(rn2);
+        // inner right-hand side r / ||r|| in float32; inner iterate from zero
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->w64, s->y32, 1.0 / rn, n);
+        CUDA_TRY(cudaGetLastError());
+        s->launches += 1;
+        CUDA_TRY(cudaMemsetAsync(s->x32, 0, n * sizeof(float2), s->st));
+        const double target = std::max(s->opt.tol_inner, 0.5 * tol / rel);
+        while (it < maxit) {
+            const int blk = std::min(s->opt.check_every, maxit - it);
+            run_iterations<float>(s, blk, adj);
+            it += blk;
+            inc = read_last_increment(s);
+            apply_operator<float>(s, adj, INV_RESID);  // inner residual (float32)
+            double ri[2];
+            read_red(s, ri);
+            const double rr = std::sqrt(ri[0] / ri[1]);
+            if (!finite(rr) || !finite(inc)) { st = CBS_EDIVERGED; break; }
+            if (rr <= target) break;
+        }
+        if (st != CBS_OK) break;
+        // x64 += ||r|| x32 ;  r = y - A_s x64  (float64)
+        k_axpy_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x64, s->x32, rn, n);
+        CUDA_TRY(cudaGetLastError());
+        s->launches += 1;
+        apply_operator<double>(s, adj, INV_RESID);
+        read_red(s, r);
+        info->residual_checks++;
+        rn2 = r[0];
+        rel = std::sqrt(rn2 / ny2);
+        ++outer;
+        if (!finite(rel)) { st = CBS_EDIVERGED; break; }
+    }
+    if (st == CBS_OK && rel > tol) st = CBS_ENOCONV;
+    info->iters = it;
+    info->outer_iters = outer;
+    info->rel_residual = rel;
+    info->rel_increment = inc;
+    return st;
+}
+
+cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void* x0, cbs_info* info_out, bool adj)
+{
+    if (!s) return CBS_EINVAL;
+    if (!src || !field) return set_err(s, CBS_EINVAL, "src and field must be device pointers");
+    cbs_info info{};
+    try {
+        begin_call(s);
+        s->hist_pos = 0;
+        s->launches = 0;
+        CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(int), s->st));
+        CUDA_TRY(cudaEventRecord(s->ev0, s->st));
+        prepare(s, src, x0, adj);
+        cbs_status st;
+        if (s->opt.precision == CBS_FP32_REFINE) st = solve_refine(s, adj, &info);
+        else if (s->opt.precision == CBS_FP32) st = solve_plain<float>(s, adj, &info);
+        else st = solve_plain<double>(s, adj, &info);
+        finish_field(s, field);
+        CUDA_TRY(cudaEventRecord(s->ev1, s->st));
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+        info.t_solve_ms = ms;
+        info.t_setup_ms = s->t_setup_ms;
+        info.a1[0] = s->a1r; info.a1[1] = s->a1i;
+        info.a2[0] = s->a2r; info.a2[1] = s->a2i;
+        info.lambda1 = s->lam1;
+        info.lambda2 = s->lam2;
+        info.kernel_launches = s->launches;
+        if (info_out) *info_out = info;
+        if (st == CBS_ENOCONV) s->err = "max_iter reached before tol";
+        if (st == CBS_EDIVERGED) s->err = "iteration produced a non-finite value";
+        return st;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    } catch (const Fail& f) {
+        return set_err(s, f.code, "allocation failed");
+    }
+}
+
+template <typename R> void fill_plan(cbs_solver* s, Plan<R>& P)
+{
+    P.d.D = s->D;
+    P.d.n0 = s->n[0];
+    P.d.n1 = s->n[1];
+    P.d.n2 = s->n[2];
+    P.d.N = s->N;
+    const bool f = std::is_same<R, float>::value;
+    for (int e = 0; e < 3; ++e) {
+        P.M.rs[e] = f ? (const R*)s->rs32[e] : (const R*)s->rs64[e];
+        P.M.gc[e] = f ? (const R*)s->gc32[e] : (const R*)s->gc64[e];
+        P.M.gs[e] = f ? (const R*)s->gs32[e] : (const R*)s->gs64[e];
+        P.Sy.kt[e] = f ? (const cplx<R>*)s->kt32[e] : (const cplx<R>*)s->kt64[e];
+        P.Sy.k2[e] = f ? (const R*)s->k232[e] : (const R*)s->k264[e];
+        P.tw[e] = f ? (const cplx<R>*)s->tw32[e] : (const cplx<R>*)s->tw64[e];
+    }
+    P.M.kp = f ? (const R*)s->kp32 : (const R*)s->kp64;
+    P.M.et = f ? (const R*)s->et32 : (const R*)s->et64;
+    P.M.omega = (R)s->omega;
+    P.M.a1r = (R)(s->a1r / s->lam1);
+    P.M.a1i = (R)(s->a1i / s->lam1);
+    P.M.a2r = (R)(s->a2r / s->lam2);
+    P.M.a2i = (R)(s->a2i / s->lam2);
+    // symbol constants (App. B.1 with a = a1, lambda_0 = lambda1, b = a2, lambda_1 = lambda2)
+    const double l1 = s->lam1, l2 = s->lam2;
+    const double apr = s->a1r + l1, api = s->a1i;   // a1 + lambda1
+    const double bpr = s->a2r + l2, bpi = s->a2i;   // a2 + lambda2
+    const double den = apr * apr + api * api;
+    const double Pr = l1 * apr / den, Pi = -l1 * api / den;  // lambda1 / (a1 + lambda1)
+    const double scale = 1.0 / (double)s->N;
+    const double sq = std::sqrt(l1 * l2);
+    P.Sy.Pu = mk<cplx<R>, R>((R)Pr, (R)Pi);
+    P.Sy.P = mk<cplx<R>, R>((R)(Pr * scale), (R)(Pi * scale));
+    P.Sy.c1 = mk<cplx<R>, R>((R)0, (R)sq);
+    P.Sy.c2 = mk<cplx<R>, R>((R)(l2 * apr), (R)(l2 * api));
+    P.Sy.c3 = mk<cplx<R>, R>((R)(apr * bpr - api * bpi), (R)(apr * bpi + api * bpr));
+    P.Sy.la1 = mk<cplx<R>, R>((R)(s->a1r / l1), (R)(s->a1i / l1));
+    P.Sy.la2 = mk<cplx<R>, R>((R)(s->a2r / l2), (R)(s->a2i / l2));
+    P.Sy.isq = (R)(1.0 / sq);
+    P.Sy.scale = (R)scale;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* cbs_last_error(const cbs_solver* s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+void solver_destroy(cbs_solver* s)
+{
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (int a = 0; a < 2; ++a) {
+        if (s->graph64[a]) cudaGraphExecDestroy(s->graph64[a]);
+        if (s->graph32[a]) cudaGraphExecDestroy(s->graph32[a]);
+    }
+    for (void* p : s->allocs) cudaFree(p);
+    if (s->host_red) cudaFreeHost(s->host_red);
+    if (s->ev_user) cudaEventDestroy(s->ev_user);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->st) cudaStreamDestroy(s->st);
+    delete s;
+}
+
+cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const double* c0, const double* rho,
+                         const double* alpha, const cbs_boundary* boundary, const cbs_options* opt, cbs_solver** out)
+{
+    if (!out) return set_err(nullptr, CBS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !c0 || !rho || !alpha) return set_err(nullptr, CBS_EINVAL, "NULL grid or medium pointer");
+    if (grid->ndim != 2 && grid->ndim != 3) return set_err(nullptr, CBS_EINVAL, "ndim must be 2 or 3");
+    for (int a = 0; a < grid->ndim; ++a)
+        if (!size_supported(grid->n[a]))
+            return set_err(nullptr, CBS_EINVAL, "unsupported extent " + std::to_string((long long)grid->n[a]));
+    if (!(dx > 0) || !(omega > 0) || !std::isfinite(dx) || !std::isfinite(omega))
+        return set_err(nullptr, CBS_EINVAL, "dx and omega must be positive");
+    cbs_options o{};
+    if (opt) o = *opt;
+    if (o.nu == 0) o.nu = 0.5;
+    if (o.beta == 0) o.beta = 0.95;
+    if (o.tol_inner == 0) o.tol_inner = 1e-4;
+    if (o.max_iter == 0) o.max_iter = 100000;
+    if (o.check_every <= 0) o.check_every = 50;
+    if (!(o.nu > 0 && o.nu < 1) || !(o.beta > 0 && o.beta < 1))
+        return set_err(nullptr, CBS_EINVAL, "nu and beta must lie in (0, 1)");
+    if (o.precision < CBS_FP64 || o.precision > CBS_FP32) return set_err(nullptr, CBS_EINVAL, "bad precision");
+    if (o.shift_rule != CBS_SHIFT_MIDRANGE && o.shift_rule != CBS_SHIFT_MEDIAN)
+        return set_err(nullptr, CBS_EINVAL, "bad shift rule");
+    cbs_boundary b{};
+    if (boundary) b = *boundary;
+    if (b.power == 0) b.power = 2.0;
+    if (!(b.gamma_max >= 0) || !std::isfinite(b.gamma_max)) return set_err(nullptr, CBS_EINVAL, "bad gamma_max");
+    for (int a = 0; a < grid->ndim; ++a)
+        for (int k = 0; k < 2; ++k)
+            if (b.n_abs[a][k] < 0 || b.n_abs[a][k] >= grid->n[a])
+                return set_err(nullptr, CBS_EINVAL, "bad absorbing layer width");
+
+    cbs_solver* s = new cbs_solver();
+    s->D = grid->ndim;
+    s->C = s->D + 1;
+    for (int a = 0; a < s->D; ++a) s->n[a] = (int)grid->n[a];
+    s->N = (long long)s->n[0] * s->n[1] * s->n[2];
+    s->dx = dx;
+    s->omega = omega;
+    s->opt = o;
+    s->bnd = b;
+    try {
+        CUDA_TRY(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreate(&s->ev0));
+        CUDA_TRY(cudaEventCreate(&s->ev1));
+        CUDA_TRY(cudaMallocHost(&s->host_red, 2 * kHistCap * sizeof(double)));
+        begin_call(s);
+        CUDA_TRY(cudaEventRecord(s->ev0, s->st));
+        const long long N = s->N;
+        const int D = s->D;
+        // per-axis tables (host, float64): gamma, wavenumbers, twiddles
+        for (int a = 0; a < 3; ++a) {
+            const int n = s->n[a];
+            std::vector<double> gc(n, 0.0), gs(n, 0.0), k2(n, 0.0);
+            std::vector<double2> kt(n), tw(n);
+            std::vector<float> gc32(n), gs32(n), k232(n);
+            std::vector<float2> kt32(n), tw32(n);
+            for (int i = 0; i < n; ++i) {
+                if (a < D) {
+                    gc[i] = layer_gamma((double)i, n, b.n_abs[a][0], b.n_abs[a][1], b.gamma_max, b.power);
+                    gs[i] = layer_gamma(i + 0.5, n, b.n_abs[a][0], b.n_abs[a][1], b.gamma_max, b.power);
+                }
+                const int f = (i < (n + 1) / 2) ? i : i - n;
+                const double k = 2.0 * kPi * f / (n * dx);
+                kt[i] = make_double2(k * std::cos(k * dx / 2), k * std::sin(k * dx / 2));
+                k2[i] = k * k;
+                const double ang = -2.0 * kPi * (double)i / (double)n;
+                tw[i] = make_double2(std::cos(ang), std::sin(ang));
+                gc32[i] = (float)gc[i];
+                gs32[i] = (float)gs[i];
+                k232[i] = (float)k2[i];
+                kt32[i] = make_float2((float)kt[i].x, (float)kt[i].y);
+                tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+            }
+            s->gc64[a] = dalloc<double>(s, n); upload(s, s->gc64[a], gc);
+            s->gs64[a] = dalloc<double>(s, n); upload(s, s->gs64[a], gs);
+            s->k264[a] = dalloc<double>(s, n); upload(s, s->k264[a], k2);
+            s->kt64[a] = dalloc<double2>(s, n); upload(s, s->kt64[a], kt);
+            s->tw64[a] = dalloc<double2>(s, n); upload(s, s->tw64[a], tw);
+            s->gc32[a] = dalloc<float>(s, n); upload(s, s->gc32[a], gc32);
+            s->gs32[a] = dalloc<float>(s, n); upload(s, s->gs32[a], gs32);
+            s->k232[a] = dalloc<float>(s, n); upload(s, s->k232[a], k232);
+            s->kt32[a] = dalloc<float2>(s, n); upload(s, s->kt32[a], kt32);
+            s->tw32[a] = dalloc<float2>(s, n); upload(s, s->tw32[a], tw32);
+            CUDA_TRY(cudaStreamSynchronize(s->st));  // host vectors go out of scope
+        }
+        SetupIn si;
+        si.D = D; si.n0 = s->n[0]; si.n1 = s->n[1]; si.n2 = s->n[2]; si.N = N; si.omega = omega;
+        si.c0 = c0; si.rho = rho; si.alpha = alpha;
+        for (int a = 0; a < 3; ++a) { si.gc[a] = s->gc64[a]; si.gs[a] = s->gs64[a]; }
+        const int sg = grid_for(N, kSetupThreads);
+        double* part = dalloc<double>(s, (size_t)sg * 8);
+        int* bad = dalloc<int>(s, 1);
+        CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s->st));
+        k_setup_minmax<<<sg, kSetupThreads, 0, s->st>>>(si, part, bad);
+        CUDA_TRY(cudaGetLastError());
+        std::vector<double> hp((size_t)sg * 8);
+        int hbad = 0;
+        CUDA_TRY(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        if (hbad) {
+            solver_destroy(s);
+            return set_err(nullptr, CBS_EINVAL, "medium rejected: non-finite value, c0 <= 0, rho <= 0 or alpha < 0");
+        }
+        if (o.shift_rule == CBS_SHIFT_MIDRANGE) {
+            double mm[8] = {INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY};
+            for (int bi = 0; bi < sg; ++bi)
+                for (int k = 0; k < 8; ++k)
+                    mm[k] = (k & 1) ? std::max(mm[k], hp[bi * 8 + k]) : std::min(mm[k], hp[bi * 8 + k]);
+            s->a1r = 0.5 * (mm[0] + mm[1]);
+            s->a1i = 0.5 * (mm[2] + mm[3]);
+            s->a2r = 0.5 * (mm[4] + mm[5]);
+            s->a2i = 0.5 * (mm[6] + mm[7]);
+        } else {
+            double2* dv = dalloc<double2>(s, (size_t)D * N);
+            double2* qv = dalloc<double2>(s, (size_t)N);
+            k_setup_values<<<sg, kSetupThreads, 0, s->st>>>(si, dv, qv);
+            CUDA_TRY(cudaGetLastError());
+            std::vector<double2> hd((size_t)D * N), hq((size_t)N);
+            CUDA_TRY(cudaMemcpyAsync(hd.data(), dv, hd.size() * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
+            CUDA_TRY(cudaMemcpyAsync(hq.data(), qv, hq.size() * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
+            CUDA_TRY(cudaStreamSynchronize(s->st));
+            auto median = [](std::vector<double>& v) {
+                const size_t m = v.size();
+                std::sort(v.begin(), v.end());
+                return (m % 2) ? v[m / 2] : 0.5 * (v[m / 2 - 1] + v[m / 2]);
+            };
+            std::vector<double> re, im;
+            re.reserve(hd.size()); im.reserve(hd.size());
+            for (auto& z : hd) { re.push_back(z.x); im.push_back(z.y); }
+            s->a1r = median(re); s->a1i = median(im);
+            re.clear(); im.clear();
+            for (auto& z : hq) { re.push_back(z.x); im.push_back(z.y); }
+            s->a2r = median(re); s->a2i = median(im);
+        }
+        k_setup_maxdev<<<sg, kSetupThreads, 0, s->st>>>(si, make_double2(s->a1r, s->a1i), make_double2(s->a2r, s->a2i), part);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(hp.data(), part, (size_t)sg * 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        double m1 = 0, m2 = 0;
+        for (int bi = 0; bi < sg; ++bi) { m1 = std::max(m1, hp[bi * 2]); m2 = std::max(m2, hp[bi * 2 + 1]); }
+        s->lam1 = m1 > 0 ? m1 / o.beta : std::hypot(s->a1r, s->a1i);
+        s->lam2 = m2 > 0 ? m2 / o.beta : std::hypot(s->a2r, s->a2i);
+        if (!(s->lam1 > 0) || !(s->lam2 > 0) || !std::isfinite(s->lam1) || !std::isfinite(s->lam2)) {
+            solver_destroy(s);
+            return set_err(nullptr, CBS_EINVAL, "degenerate scaling: a diagonal block is identically zero");
+        }
+        for (int e = 0; e < 3; ++e) {
+            s->rs64[e] = dalloc<double>(s, e < D ? N : 1);
+            s->rs32[e] = dalloc<float>(s, e < D ? N : 1);
+        }
+        s->kp64 = dalloc<double>(s, N); s->et64 = dalloc<double>(s, N);
+        s->kp32 = dalloc<float>(s, N); s->et32 = dalloc<float>(s, N);
+        k_setup_store<<<sg, kSetupThreads, 0, s->st>>>(si, 1.0 / s->lam1, 1.0 / s->lam2, s->rs64[0], s->rs64[1],
+                                                       s->rs64[2], s->kp64, s->et64, s->rs32[0], s->rs32[1],
+                                                       s->rs32[2], s->kp32, s->et32);
+        CUDA_TRY(cudaGetLastError());
+        // working fields
+        const long long n = (long long)s->C * N;
+        s->x64 = dalloc<double2>(s, n);
+        s->y64 = dalloc<double2>(s, n);
+        s->w64 = dalloc<double2>(s, n);
+        if (o.precision != CBS_FP64) {
+            s->x32 = dalloc<float2>(s, n);
+            s->y32 = dalloc<float2>(s, n);
+            s->w32 = dalloc<float2>(s, n);
+        }
+        fill_plan<double>(s, s->P64);
+        fill_plan<float>(s, s->P32);
+        const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)), grid_for(n));
+        s->npart = nb;
+        s->partials = dalloc<double>(s, (size_t)nb * 2);
+        s->red = dalloc<double>(s, 2);
+        s->hist = dalloc<double>(s, (size_t)kHistCap * 2);
+        s->counter = dalloc<int>(s, 1);
+        CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(int), s->st));
+        CUDA_TRY(cudaEventRecord(s->ev1, s->st));
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+        s->t_setup_ms = ms;
+    } catch (const CudaError& e) {
+        std::string msg = std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what;
+        solver_destroy(s);
+        return set_err(nullptr, CBS_ECUDA, msg);
+    } catch (const Fail& f) {
+        solver_destroy(s);
+        return set_err(nullptr, f.code, "device allocation failed");
+    }
+    *out = s;
+    return CBS_OK;
+}
+
+cbs_status solve_forward(cbs_solver* s, const void* src, void* field, const void* x0, cbs_info* info)
+{
+    return solve_common(s, src, field, x0, info, false);
+}
+
+cbs_status solve_adjoint(cbs_solver* s, const void* src, void* field, const void* x0, cbs_info* info)
+{
+    return solve_common(s, src, field, x0, info, true);
+}
+
+cbs_status residual_norm(cbs_solver* s, const void* field, const void* src, int adjoint, double* rel)
+{
+    if (!s) return CBS_EINVAL;
+    if (!field || !src || !rel) return set_err(s, CBS_EINVAL, "NULL argument");
+    try {
+        begin_call(s);
+        prepare(s, src, field, adjoint != 0);
+        apply_operator<double>(s, adjoint != 0, INV_RESID);
+        double r[2];
+        read_red(s, r);
+        *rel = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status born_iterate(cbs_solver* s, const void* y, void* x, int n_iter, int adjoint, double* incr)
+{
+    if (!s) return CBS_EINVAL;
+    if (!y || !x || n_iter < 0) return set_err(s, CBS_EINVAL, "bad argument");
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        s->hist_pos = 0;
+        CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(int), s->st));
+        const bool f32 = s->opt.precision != CBS_FP64;
+        if (f32) {
+            k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)y, s->y32, 1.0, n);
+            k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)x, s->x32, 1.0, n);
+            CUDA_TRY(cudaGetLastError());
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(s->y64, y, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+            CUDA_TRY(cudaMemcpyAsync(s->x64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        }
+        int done = 0;
+        while (done < n_iter) {
+            const int blk = std::min(kHistCap, n_iter - done);
+            for (int k = 0; k < blk; ++k) {
+                if (f32) iterate_once<float>(s, adjoint != 0);
+                else iterate_once<double>(s, adjoint != 0);
+            }
+            if (incr) {
+                CUDA_TRY(cudaMemcpyAsync(s->host_red, s->hist, 2 * kHistCap * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+                CUDA_TRY(cudaStreamSynchronize(s->st));
+                for (int k = 0; k < blk; ++k) {
+                    const int j = (done + k) % kHistCap;
+                    const double a = s->host_red[2 * j], b = s->host_red[2 * j + 1];
+                    incr[done + k] = b > 0 ? std::sqrt(a / b) : 0.0;
+                }
+            }
+            done += blk;
+        }
+        if (f32) k_cast_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x32, (double2*)x, n);
+        else CUDA_TRY(cudaMemcpyAsync(x, s->x64, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status green_apply(cbs_solver* s, const void* in, void* out, int adjoint)
+{
+    if (!s) return CBS_EINVAL;
+    if (!in || !out) return set_err(s, CBS_EINVAL, "NULL argument");
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        if (s->opt.precision != CBS_FP64) {
+            k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)in, s->x32, 1.0, n);
+            CUDA_TRY(cudaGetLastError());
+            apply_green<float>(s, adjoint != 0);
+            k_cast_32_64<<<grid_for(n), 256, 0, s->st>>>(s->w32, (double2*)out, n);
+            CUDA_TRY(cudaGetLastError());
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(s->x64, in, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+            apply_green<double>(s, adjoint != 0);
+            CUDA_TRY(cudaMemcpyAsync(out, s->w64, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        }
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status operator_apply(cbs_solver* s, const void* x, void* out, int adjoint)
+{
+    if (!s) return CBS_EINVAL;
+    if (!x || !out) return set_err(s, CBS_EINVAL, "NULL argument");
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        CUDA_TRY(cudaMemcpyAsync(s->x64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        apply_operator<double>(s, adjoint != 0, INV_APPLY);
+        CUDA_TRY(cudaMemcpyAsync(out, s->w64, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status scale_source(cbs_solver* s, const void* src, void* y, int adjoint)
+{
+    if (!s) return CBS_EINVAL;
+    if (!src || !y) return set_err(s, CBS_EINVAL, "NULL argument");
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        k_scale_source<<<grid_for(n), 256, 0, s->st>>>(scale_in(s), (const double2*)src, (double2*)y, adjoint ? 1 : 0);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status unscale_field(cbs_solver* s, const void* x, void* field)
+{
+    if (!s) return CBS_EINVAL;
+    if (!x || !field) return set_err(s, CBS_EINVAL, "NULL argument");
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        k_scale_blocks<<<grid_for(n), 256, 0, s->st>>>(s->D, s->N, 1.0 / std::sqrt(s->lam1), 1.0 / std::sqrt(s->lam2),
+                                                       (const double2*)x, (double2*)field);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status solver_scalars(const cbs_solver* s, double* out)
+{
+    if (!s || !out) return CBS_EINVAL;
+    out[0] = s->a1r; out[1] = s->a1i; out[2] = s->a2r; out[3] = s->a2i; out[4] = s->lam1; out[5] = s->lam2;
+    return CBS_OK;
+}
+
+cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter, char* names, int names_len,
+                               double* ms, int max_k, int* nk)
+{
+    if (!s) return CBS_EINVAL;
+    if (!y || !x || n_iter <= 0 || !ms || !nk) return set_err(s, CBS_EINVAL, "bad argument");
+    const bool f32 = s->opt.precision != CBS_FP64;
+    const char* kn3[6] = {"rows_fwd", "axis_fwd", "last_symbol", "axis_inv", "rows_inv", "reduce"};
+    const char* kn2[4] = {"rows_fwd", "last_symbol", "rows_inv", "reduce"};
+    const int K = s->D == 3 ? 6 : 4;
+    const char** kn = s->D == 3 ? kn3 : kn2;
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        if (f32) {
+            k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)y, s->y32, 1.0, n);
+            k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)x, s->x32, 1.0, n);
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(s->y64, y, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+            CUDA_TRY(cudaMemcpyAsync(s->x64, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        }
+        std::vector<cudaEvent_t> ev(K + 1);
+        for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+        std::vector<double> acc(K, 0.0);
+        for (int it = 0; it < n_iter; ++it) {
+            int k = 0;
+            auto mark = [&]() { CUDA_TRY(cudaEventRecord(ev[k++], s->st)); };
+            mark();
+            if (f32) {
+                Plan<float>& P = s->P32;
+                CUDA_TRY(launch_rows_fwd<float>(P, s->x32, s->y32, s->w32, FWD_BORN, 0, s->st)); mark();
+                if (s->D == 3) { CUDA_TRY(launch_axis<float>(P, s->w32, -1, s->st)); mark(); }
+                CUDA_TRY(launch_last<float>(P, s->w32, SYM_GREEN, s->st)); mark();
+                if (s->D == 3) { CUDA_TRY(launch_axis<float>(P, s->w32, +1, s->st)); mark(); }
+                CUDA_TRY(launch_rows_inv<float>(P, s->x32, s->y32, s->w32, INV_BORN, 0, (float)s->opt.nu, s->partials, s->st)); mark();
+                reduce<float>(s, rows_blocks<float>(P), false); mark();
+            } else {
+                Plan<double>& P = s->P64;
+                CUDA_TRY(launch_rows_fwd<double>(P, s->x64, s->y64, s->w64, FWD_BORN, 0, s->st)); mark();
+                if (s->D == 3) { CUDA_TRY(launch_axis<double>(P, s->w64, -1, s->st)); mark(); }
+                CUDA_TRY(launch_last<double>(P, s->w64, SYM_GREEN, s->st)); mark();
+                if (s->D == 3) { CUDA_TRY(launch_axis<double>(P, s->w64, +1, s->st)); mark(); }
+                CUDA_TRY(launch_rows_inv<double>(P, s->x64, s->y64, s->w64, INV_BORN, 0, s->opt.nu, s->partials, s->st)); mark();
+                reduce<double>(s, rows_blocks<double>(P), false); mark();
+            }
+            CUDA_TRY(cudaStreamSynchronize(s->st));
+            for (int j = 0; j < K; ++j) {
+                float t = 0;
+                CUDA_TRY(cudaEventElapsedTime(&t, ev[j], ev[j + 1]));
+                acc[j] += t;
+            }
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        const int m = std::min(K, max_k);
+        for (int j = 0; j < m; ++j) ms[j] = acc[j] / n_iter;
+        *nk = m;
+        if (names && names_len > 0) {
+            std::string all;
+            for (int j = 0; j < m; ++j) { all += kn[j]; all.push_back('\0'); }
+            std::memcpy(names, all.data(), std::min((size_t)names_len, all.size()));
+        }
+        if (f32) k_cast_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x32, (double2*)x, n);
+        else CUDA_TRY(cudaMemcpyAsync(x, s->x64, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+}  // extern "C"

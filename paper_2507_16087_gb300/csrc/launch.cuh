@@ -1,0 +1,196 @@
+// launch.cuh -- host-side launchers of the Born kernels for one precision.
+// Each launcher dispatches on the axis extent to the kernel instantiated for
+// that size (the FFT plans are compile-time).  Included by exactly one
+// translation unit per precision (kernels_f32.cu, kernels_f64.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "born.cuh"
+
+namespace cbs {
+
+// Elements per thread of one transform (RX for row/axis kernels, RL for the
+// all-components pencil kernel, which keeps C transforms in registers).
+template <typename R> __host__ __device__ constexpr int r_rows(int n) { return (n % 3 == 0) ? 12 : 8; }
+template <typename R> __host__ __device__ constexpr int r_last(int n)
+{
+    return sizeof(R) == 4 ? ((n % 3 == 0) ? 6 : 8) : ((n % 3 == 0) ? 6 : 4);
+}
+template <typename R> __host__ __device__ constexpr int cols_axis(int n)
+{
+    return sizeof(R) == 4 ? (n <= 256 ? 16 : 8) : (n <= 128 ? 8 : 4);
+}
+template <typename R> __host__ __device__ constexpr int cols_last(int n)
+{
+    return sizeof(R) == 4 ? (n <= 128 ? 16 : (n <= 256 ? 8 : 4)) : (n <= 128 ? 8 : (n <= 256 ? 4 : 2));
+}
+
+#define CBS_FOR_EACH_SIZE(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512)
+
+inline bool size_supported(long long n)
+{
+    switch (n) {
+#define CBS_CASE(n) case n:
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+        return true;
+    default:
+        return false;
+    }
+}
+
+template <typename R> struct Plan {
+    Dims d;
+    Medium<R> M;
+    Symbol<R> Sy;
+    const cplx<R>* tw[3];  // twiddle table of each axis length
+};
+
+template <typename R> inline int rows_blocks(const Plan<R>& P)
+{
+    int n0 = P.d.n0;
+    long long rows = (long long)(P.d.D + 1) * (P.d.N / n0);
+    int per = 1;
+    switch (n0) {
+#define CBS_CASE(n) case n: per = RowCfg<R, n, r_rows<R>(n)>::ROWS; break;
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return 0;
+    }
+    return (int)((rows + per - 1) / per);
+}
+
+template <typename R, int N> cudaError_t rows_fwd_n(const Plan<R>& P, const cplx<R>* x, const cplx<R>* y, cplx<R>* w,
+                                                    int mode, int adj, cudaStream_t st)
+{
+    constexpr int RX = r_rows<R>(N);
+    using Cfg = RowCfg<R, N, RX>;
+    long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
+    int grid = (int)((rows + Cfg::ROWS - 1) / Cfg::ROWS);
+    k_rows_fwd<R, N, RX><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj);
+    return cudaGetLastError();
+}
+
+template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x, const cplx<R>* y, cplx<R>* w, int mode,
+                                                    int adj, R nu, double* partials, cudaStream_t st)
+{
+    constexpr int RX = r_rows<R>(N);
+    using Cfg = RowCfg<R, N, RX>;
+    long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
+    int grid = (int)((rows + Cfg::ROWS - 1) / Cfg::ROWS);
+    k_rows_inv<R, N, RX><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj, nu, partials);
+    return cudaGetLastError();
+}
+
+template <typename R, int N, int S> cudaError_t axis_n(const Plan<R>& P, cplx<R>* w, cudaStream_t st)
+{
+    constexpr int RA = r_rows<R>(N);
+    constexpr int COLS = cols_axis<R>(N);
+    constexpr int T = N / RA;
+    const size_t smem = (size_t)N * COLS * sizeof(cplx<R>);
+    auto kern = k_axis_fft<R, N, RA, COLS, S>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int xblocks = (P.d.n0 + COLS - 1) / COLS;
+    long long grid = (long long)(P.d.D + 1) * P.d.n2 * xblocks;
+    kern<<<(unsigned)grid, T * COLS, smem, st>>>(P.d, w, P.tw[1]);
+    return cudaGetLastError();
+}
+
+template <typename R, int N, int C> cudaError_t last_n(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st)
+{
+    constexpr int RL = r_last<R>(N);
+    constexpr int COLS = cols_last<R>(N);
+    constexpr int T = N / RL;
+    const size_t smem = (size_t)C * N * COLS * sizeof(cplx<R>);
+    auto kern = k_last_symbol<R, N, RL, COLS, C>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int xblocks = (P.d.n0 + COLS - 1) / COLS;
+    long long grid = (long long)(C == 4 ? P.d.n1 : 1) * xblocks;
+    kern<<<(unsigned)grid, T * COLS, smem, st>>>(P.d, P.Sy, w, P.tw[P.d.D - 1], mode);
+    return cudaGetLastError();
+}
+
+template <typename R> cudaError_t launch_rows_fwd(const Plan<R>& P, const cplx<R>* x, const cplx<R>* y, cplx<R>* w,
+                                                  int mode, int adj, cudaStream_t st)
+{
+    switch (P.d.n0) {
+#define CBS_CASE(n) case n: return rows_fwd_n<R, n>(P, x, y, w, mode, adj, st);
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R> cudaError_t launch_rows_inv(const Plan<R>& P, cplx<R>* x, const cplx<R>* y, cplx<R>* w, int mode,
+                                                  int adj, R nu, double* partials, cudaStream_t st)
+{
+    switch (P.d.n0) {
+#define CBS_CASE(n) case n: return rows_inv_n<R, n>(P, x, y, w, mode, adj, nu, partials, st);
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R> cudaError_t launch_axis(const Plan<R>& P, cplx<R>* w, int sign, cudaStream_t st)
+{
+    switch (P.d.n1) {
+#define CBS_CASE(n) case n: return sign < 0 ? axis_n<R, n, -1>(P, w, st) : axis_n<R, n, +1>(P, w, st);
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R> cudaError_t launch_last(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st)
+{
+    const int nl = P.d.D == 3 ? P.d.n2 : P.d.n1;
+    if (P.d.D == 3) {
+        switch (nl) {
+#define CBS_CASE(n) case n: return last_n<R, n, 4>(P, w, mode, st);
+            CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (nl) {
+#define CBS_CASE(n) case n: return last_n<R, n, 3>(P, w, mode, st);
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// explicit instantiation helper
+#define CBS_INSTANTIATE_LAUNCHERS(R)                                                                                 \
+    template int rows_blocks<R>(const Plan<R>&);                                                                     \
+    template cudaError_t launch_rows_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int, int,      \
+                                            cudaStream_t);                                                           \
+    template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R, double*, \
+                                            cudaStream_t);                                                           \
+    template cudaError_t launch_axis<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                                \
+    template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);
+
+}  // namespace cbs
+
+namespace cbs {
+// declarations for translation units that only call the launchers
+#define CBS_EXTERN_LAUNCHERS(R)                                                                                      \
+    extern template int rows_blocks<R>(const Plan<R>&);                                                              \
+    extern template cudaError_t launch_rows_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int, int, \
+                                                   cudaStream_t);                                                    \
+    extern template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R,   \
+                                                   double*, cudaStream_t);                                           \
+    extern template cudaError_t launch_axis<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                         \
+    extern template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);
+}  // namespace cbs

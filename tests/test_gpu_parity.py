@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle,
+element by element on the same seeded inputs.
+
+Tolerances (relative L2 unless stated):
+  FP64 path: set-up scalars 1e-13; source scaling 1e-14; one (L+I)^-1 or A_s
+  apply 1e-12 (FFT rounding ~ eps log N); 20-50 Born iterations 1e-11; converged
+  solves run to residual 1e-12 on both sides 1e-10.
+  FP32 path: one apply 2e-6 (float32 eps * log N * a few); FP32 + FP64
+  refinement converged to residual <= 1e-8: 1e-5 against the oracle.
+Sizes span several FFT tiles and ragged edges: extents 8..192 with factors 2
+and 3, grids whose x extent is smaller than a block's column tile, and 2D/3D.
+"""
+import numpy as np
+import pytest
+
+from oracle import dense
+from oracle import oracle as O
+from paper_2507_16087_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _cbs():
+    from paper_2507_16087_gb300 import cbs
+    return cbs
+
+
+DEV = "cuda:0"
+
+
+def T(a, dt=None):
+    a = np.ascontiguousarray(a)
+    if dt is None:
+        dt = torch.complex128 if np.iscomplexobj(a) else torch.float64
+    return torch.tensor(a, dtype=dt, device=DEV).contiguous()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make(shape, seed=1, n_abs=3, gamma_scale=0.5, precision="fp64", **kw):
+    p = W.smooth_random_medium(shape, seed=seed, n_abs=n_abs)
+    p.gamma_max = gamma_scale * p.omega
+    cbs = _cbs()
+    s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max, precision=precision, **kw)
+    P = O.Problem(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max)
+    return p, s, P
+
+
+SHAPES = [(16, 16), (24, 32), (96, 64), (12, 48), (8, 8, 8), (16, 24, 12), (12, 16, 32), (24, 8, 96)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_setup_scalars_match(shape):
+    _, s, P = make(shape, seed=3)
+    g, o = s.scalars(), P.scalars()
+    for k in ("a1", "a2", "lambda1", "lambda2"):
+        assert abs(g[k] - o[k]) <= 1e-13 * abs(o[k]), (k, g[k], o[k])
+
+
+@pytest.mark.parametrize("shape", [(24, 32), (16, 24, 12)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_scale_source_matches(shape, adjoint):
+    _, s, P = make(shape, seed=4)
+    src = W.random_source(shape, 5)
+    y = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.scale_source(T(src), y, adjoint)
+    assert rel(y.cpu().numpy(), P.scale_source(src, adjoint)) <= 1e-14
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(128, 128), (64, 64, 64)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_green_apply_fp64(shape, adjoint):
+    _, s, P = make(shape, seed=6)
+    v = W.random_source(shape, 7)
+    out = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.green_apply(T(v), out, adjoint)
+    ref = P.green(v, adjoint)
+    assert rel(out.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(24, 32), (96, 64), (16, 24, 12), (64, 64, 64)])
+def test_green_apply_fp32(shape):
+    _, s, P = make(shape, seed=8, precision="fp32")
+    v = W.random_source(shape, 9)
+    out = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.green_apply(T(v), out)
+    assert rel(out.cpu().numpy(), P.green(v)) <= 2e-6
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_operator_apply_fp64(shape, adjoint):
+    _, s, P = make(shape, seed=10)
+    x = W.random_source(shape, 11)
+    out = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.operator_apply(T(x), out, adjoint)
+    assert rel(out.cpu().numpy(), P.apply(x, adjoint)) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_born_iterations_fp64(shape, adjoint):
+    _, s, P = make(shape, seed=12)
+    y = P.scale_source(W.random_source(shape, 13), adjoint)
+    x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    inc = s.born_iterate(T(y), x, 40, adjoint)
+    xr, incr = P.iterate(y, n_iter=40, nu=0.5, adjoint=adjoint)
+    assert rel(x.cpu().numpy(), xr) <= 1e-11
+    assert np.allclose(inc, incr, rtol=1e-9, atol=0)
+
+
+def test_born_iterations_fp32():
+    shape = (16, 24, 32)
+    _, s, P = make(shape, seed=14, precision="fp32")
+    y = P.scale_source(W.random_source(shape, 15))
+    x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.born_iterate(T(y), x, 30)
+    xr, _ = P.iterate(y, n_iter=30, nu=0.5)
+    assert rel(x.cpu().numpy(), xr) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(24, 32), (16, 12, 8)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_converged_solve_fp64_matches_oracle_and_dense(shape, adjoint):
+    p, s, P = make(shape, seed=16, tol=1e-12, check_every=20)
+    src = W.random_source(shape, 17)
+    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    info = (s.solve_adjoint if adjoint else s.solve_forward)(T(src), field)
+    assert info["rel_residual"] <= 1e-12
+    y = P.scale_source(src, adjoint)
+    x, _, res = P.solve(y, 1e-12, check_every=20, adjoint=adjoint)
+    got = field.cpu().numpy()
+    assert rel(got, P.unscale(x)) <= 1e-10
+    if adjoint:
+        ref = dense.solve_adjoint(src, p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power)
+    else:
+        ref = dense.solve(src, p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power)
+    assert rel(got, ref) <= 1e-10
+    # the residual entry point agrees with the solver's own report
+    r = s.residual_norm(field, T(src), adjoint)
+    assert r <= 1.5e-12
+
+
+@pytest.mark.parametrize("shape", [(96, 64), (16, 24, 32)])
+def test_fp32_refine_matches_oracle(shape):
+    p, s, P = make(shape, seed=18, precision="fp32_refine", tol=1e-8, check_every=20)
+    src = W.random_source(shape, 19)
+    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    info = s.solve_forward(T(src), field)
+    assert info["rel_residual"] <= 1e-8 and info["outer_iters"] >= 1
+    ref, _, _ = P.solve_field(src, 1e-12, check_every=25)
+    assert rel(field.cpu().numpy(), ref) <= 1e-5
+    assert s.residual_norm(field, T(src)) <= 1.01e-8
+
+
+def test_fp32_refine_residual_1e6_error_stated():
+    """North-star pairing: mixed path run to residual 1e-6 -> error vs the FP64 oracle <= 1e-5."""
+    shape = (64, 64)
+    p, s, P = make(shape, seed=20, precision="fp32_refine", tol=1e-6, check_every=20, n_abs=8)
+    src = W.random_source(shape, 21)
+    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    info = s.solve_forward(T(src), field)
+    assert info["rel_residual"] <= 1e-6
+    ref, _, _ = P.solve_field(src, 1e-12, check_every=25)
+    assert rel(field.cpu().numpy(), ref) <= 1e-5
+
+
+# ------------------------------------------------------------------- edge cases
+def test_zero_source_gives_zero_field():
+    shape = (16, 16)
+    _, s, _ = make(shape, tol=1e-8)
+    field = torch.ones(s.field_shape, dtype=torch.complex128, device=DEV)
+    info = s.solve_forward(torch.zeros_like(field), field)
+    assert torch.count_nonzero(field).item() == 0 and info["rel_residual"] == 0
+
+
+def test_warm_start_and_noconv():
+    shape = (24, 32)
+    cbs = _cbs()
+    p, s, P = make(shape, seed=22, tol=1e-10, max_iter=40, check_every=20)
+    src = T(W.random_source(shape, 23))
+    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    info = s.solve_forward(src, field, allow_noconv=True)
+    assert info["status"] == "CBS_ENOCONV" and info["iters"] == 40
+    with pytest.raises(cbs.CBSError):
+        s.solve_forward(src, field)
+    # resuming from the returned field continues the same iteration
+    f2 = torch.zeros_like(field)
+    s.solve_forward(src, f2, x0=field.clone(), allow_noconv=True)
+    y = P.scale_source(src.cpu().numpy())
+    x, _ = P.iterate(y, n_iter=80, nu=0.5)
+    assert rel(f2.cpu().numpy(), P.unscale(x)) <= 1e-11
+
+
+def test_rejects_invalid_media_and_sizes():
+    cbs = _cbs()
+    shape = (16, 16)
+    c0 = np.full(shape, 1500.0)
+    rho = np.full(shape, 1000.0)
+    al = np.zeros(shape)
+    for bad in ("c", "rho", "alpha", "nan"):
+        c, r, a = c0.copy(), rho.copy(), al.copy()
+        if bad == "c":
+            c[3, 3] = -1
+        elif bad == "rho":
+            r[0, 0] = 0
+        elif bad == "alpha":
+            a[5, 5] = -0.1
+        else:
+            c[2, 7] = np.nan
+        with pytest.raises(cbs.CBSError) as e:
+            cbs.solver_create(T(c), T(r), T(a), 1e-3, 3e6, [[2, 2], [2, 2]], 1e6)
+        assert e.value.status == cbs.CBS_EINVAL
+    with pytest.raises(cbs.CBSError):
+        cbs.solver_create(T(np.full((10, 16), 1500.0)), T(np.full((10, 16), 1e3)), T(np.zeros((10, 16))), 1e-3, 3e6,
+                          [[1, 1], [1, 1]], 1e6)
+    with pytest.raises(cbs.CBSError):
+        cbs.solver_create(T(c0), T(rho), T(al), 1e-3, 3e6, [[1, 1], [1, 1]], 1e6, nu=1.5)
+
+
+def test_deterministic_reruns():
+    shape = (12, 16, 32)
+    _, s, P = make(shape, seed=24, precision="fp32_refine", tol=1e-7, check_every=10)
+    src = T(W.random_source(shape, 25))
+    f1 = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    f2 = torch.zeros_like(f1)
+    i1 = s.solve_forward(src, f1)
+    i2 = s.solve_forward(src, f2)
+    assert torch.equal(f1, f2) and i1["iters"] == i2["iters"]
+
+
+# -------------------------------------------------- full-size properties (128^3)
+def test_uniform_medium_closed_form_full_size():
+    """Uniform absorbing medium without a layer: exact per-wavenumber solution at 128^3."""
+    cbs = _cbs()
+    shape = (128, 128, 128)
+    dx = W.grid_step(6.0)
+    om = 2 * np.pi * W.F0
+    al = 60.0
+    c0, rho, alpha = np.full(shape, 1500.0), np.full(shape, 1000.0), np.full(shape, al)
+    src = np.zeros((4,) + shape, dtype=np.complex128)
+    src[3, 64, 64, 30] = 1.0
+    src[0, 40, 70, 64] = 0.5j
+    ref = dense.uniform_solve(src, 1500.0, 1000.0, al, dx, om)
+    for prec, tol, bound in (("fp64", 1e-11, 1e-9), ("fp32_refine", 1e-9, 1e-7)):
+        s = cbs.solver_create(T(c0), T(rho), T(alpha), dx, om, [[0, 0]] * 3, 0.0, precision=prec, tol=tol,
+                              check_every=50)
+        field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+        s.solve_forward(T(src), field)
+        assert rel(field.cpu().numpy(), ref) <= bound, prec
+        s.destroy()
+
+
+def test_sphere_128_first_iterations_and_precisions():
+    """Full-size sphere workload (128^3, 20-cell layer, point source): the first iterations match the
+    oracle; FP32+refinement and FP64 solves to 1e-6 agree; the true residual is recomputed."""
+    cbs = _cbs()
+    p = W.sphere_128()
+    src = p.source
+    s64 = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max, precision="fp64",
+                            tol=1e-6, check_every=50)
+    P = O.Problem(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max)
+    y = P.scale_source(src)
+    x = torch.zeros(s64.field_shape, dtype=torch.complex128, device=DEV)
+    s64.born_iterate(T(y), x, 3)
+    xr, _ = P.iterate(y, n_iter=3, nu=0.5)
+    assert rel(x.cpu().numpy(), xr) <= 1e-12
+    f64 = torch.zeros(s64.field_shape, dtype=torch.complex128, device=DEV)
+    i64 = s64.solve_forward(T(src), f64)
+    s32 = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max,
+                            precision="fp32_refine", tol=1e-6, check_every=50)
+    f32 = torch.zeros_like(f64)
+    i32 = s32.solve_forward(T(src), f32)
+    assert i64["rel_residual"] <= 1e-6 and i32["rel_residual"] <= 1e-6
+    assert s64.residual_norm(f32, T(src)) <= 1.01e-6
+    assert s64.residual_norm(f64, T(src)) <= 1.01e-6
+    # both are within the stopping tolerance of the same solution
+    assert rel(f32.cpu().numpy(), f64.cpu().numpy()) <= 1e-4
