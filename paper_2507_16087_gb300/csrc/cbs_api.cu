@@ -9,6 +9,7 @@
 #include <type_traits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,6 +31,17 @@ constexpr int kSetupThreads = 256;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 thread_local std::string g_create_error = "no error";
+
+bool trace_on()
+{
+    static int on = -1;
+    if (on < 0) on = std::getenv("CBS_TRACE") != nullptr;
+    return on == 1;
+}
+#define TRACE(...)                                                                                                   \
+    do {                                                                                                             \
+        if (trace_on()) { std::fprintf(stderr, "[cbs] " __VA_ARGS__); std::fprintf(stderr, "\n"); std::fflush(stderr); } \
+    } while (0)
 
 // ---------------------------------------------------------------- set-up kernels
 struct SetupIn {
@@ -860,12 +872,16 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
     s->opt = o;
     s->bnd = b;
     try {
+        TRACE("create: stream");
         CUDA_TRY(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+        TRACE("create: events");
         CUDA_TRY(cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreate(&s->ev0));
         CUDA_TRY(cudaEventCreate(&s->ev1));
         CUDA_TRY(cudaMallocHost(&s->host_red, 2 * kHistCap * sizeof(double)));
+        TRACE("create: begin_call");
         begin_call(s);
+        TRACE("create: tables");
         CUDA_TRY(cudaEventRecord(s->ev0, s->st));
         const long long N = s->N;
         const int D = s->D;
@@ -909,6 +925,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         si.D = D; si.n0 = s->n[0]; si.n1 = s->n[1]; si.n2 = s->n[2]; si.N = N; si.omega = omega;
         si.c0 = c0; si.rho = rho; si.alpha = alpha;
         for (int a = 0; a < 3; ++a) { si.gc[a] = s->gc64[a]; si.gs[a] = s->gs64[a]; }
+        TRACE("create: minmax");
         const int sg = grid_for(N, kSetupThreads);
         double* part = dalloc<double>(s, (size_t)sg * 8);
         int* bad = dalloc<int>(s, 1);
@@ -920,6 +937,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         CUDA_TRY(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
         CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s->st));
         CUDA_TRY(cudaStreamSynchronize(s->st));
+        TRACE("create: minmax done bad=%d", hbad);
         if (hbad) {
             solver_destroy(s);
             return set_err(nullptr, CBS_EINVAL, "medium rejected: non-finite value, c0 <= 0, rho <= 0 or alpha < 0");
@@ -955,6 +973,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             for (auto& z : hq) { re.push_back(z.x); im.push_back(z.y); }
             s->a2r = median(re); s->a2i = median(im);
         }
+        TRACE("create: maxdev");
         k_setup_maxdev<<<sg, kSetupThreads, 0, s->st>>>(si, make_double2(s->a1r, s->a1i), make_double2(s->a2r, s->a2i), part);
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaMemcpyAsync(hp.data(), part, (size_t)sg * 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -967,6 +986,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             solver_destroy(s);
             return set_err(nullptr, CBS_EINVAL, "degenerate scaling: a diagonal block is identically zero");
         }
+        TRACE("create: store lam1=%g lam2=%g", s->lam1, s->lam2);
         for (int e = 0; e < 3; ++e) {
             s->rs64[e] = dalloc<double>(s, e < D ? N : 1);
             s->rs32[e] = dalloc<float>(s, e < D ? N : 1);
@@ -987,10 +1007,12 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             s->y32 = dalloc<float2>(s, n);
             s->w32 = dalloc<float2>(s, n);
         }
+        TRACE("create: plans");
         fill_plan<double>(s, s->P64);
         fill_plan<float>(s, s->P32);
         const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)), grid_for(n));
         s->npart = nb;
+        TRACE("create: partials %d", nb);
         s->partials = dalloc<double>(s, (size_t)nb * 2);
         s->red = dalloc<double>(s, 2);
         s->hist = dalloc<double>(s, (size_t)kHistCap * 2);

@@ -25,7 +25,7 @@ template <typename CT> struct real_of;
 template <> struct real_of<float2> { using T = float; };
 template <> struct real_of<double2> { using T = double; };
 
-template <typename CT, typename R> __device__ __forceinline__ CT mk(R a, R b) { CT c; c.x = a; c.y = b; return c; }
+template <typename CT, typename R> __host__ __device__ __forceinline__ CT mk(R a, R b) { CT c; c.x = a; c.y = b; return c; }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
