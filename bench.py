@@ -151,8 +151,7 @@ def kernel_bytes_per_voxel(D=3, fp=4):
     medium = D * fp + 2 * fp  # rs_eta per velocity component + (kp, et) for pressure
     return {"rows_fwd": C * cb * 3 + medium,   # x, y in; w out
             "axis_fwd": C * cb * 2, "last_symbol": C * cb * 2, "axis_inv": C * cb * 2,
-            "rows_inv": C * cb * 3 + medium,   # w, x in; x out
-            "reduce": 0}
+            "rows_inv": C * cb * 3 + medium}   # w, x in; x out
 
 
 def run_gpu(args):
@@ -294,6 +293,28 @@ def run_gpu(args):
     return 0
 
 
+def run_kernels(args):
+    """Per-kernel device times of FP32 Born iterations on the bench workload (a short command for
+    profilers); prints one JSON line."""
+    import torch
+
+    from paper_2507_16087_gb300 import cbs, workloads as W
+
+    dev = torch.device("cuda", 0)
+    p = W.sphere_128()
+    T = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    prec = "fp64" if args.precision == "fp64" else "fp32_refine"
+    s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max, precision=prec, tol=TOL)
+    src = T(p.source, torch.complex128)
+    y = torch.zeros((4,) + p.shape, dtype=torch.complex128, device=dev)
+    s.scale_source(src, y)
+    x = torch.zeros_like(y)
+    kt = s.time_kernels(y, x, args.iters)
+    s.destroy()
+    print(json.dumps({"mode": "kernels", "precision": prec, "iters": args.iters, "kernel_ms": kt}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,7 +325,12 @@ def main():
     ap.add_argument("--tol-inner", type=float, default=1e-4)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"])
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
+    if args.mode == "kernels":
+        return run_kernels(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

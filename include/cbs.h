@@ -156,7 +156,9 @@ cbs_status unscale_field(cbs_solver* s, const void* x, void* field);
 /* Shifts and scaling: out[0..5] = Re a1, Im a1, Re a2, Im a2, lambda1, lambda2. */
 cbs_status solver_scalars(const cbs_solver* s, double* out);
 
-/* Average device time (ms) per launch of each kernel of one Born iteration,
+/* Average device time (ms) per launch of each kernel of one Born iteration
+ * (the per-block norm reduction, one launch per check_every iterations, is not
+ * included),
  * measured with CUDA events on the solver's stream over n_iter iterations
  * (scaled iterate and source taken as given, updated in place).  names
  * receives up to max_k NUL-separated kernel names; ms receives one time per

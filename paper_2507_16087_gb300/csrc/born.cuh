@@ -221,34 +221,43 @@ k_rows_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restri
     CT v[RX];
 #pragma unroll
     for (int s = 0; s < RX; ++s) v[s] = w[fbase + t + T * slot_q<NX, RX, 0>(s)];
+    // issue the epilogue's loads (x, B, y at the output positions) before the
+    // transform so their latency overlaps it
+    CT xv[RX], bv[RX], yv[RX];
+    if (mode != INV_PLAIN) {
+#pragma unroll
+        for (int s = 0; s < RX; ++s) {
+            const int i0 = t + T * slot_q<NX, RX, np>(s);
+            xv[s] = x[fbase + i0];
+            bv[s] = born_B(M, rb, i0, adj != 0);
+            if (mode == INV_RESID) yv[s] = y[fbase + i0];
+        }
+    }
     fft_run<NX, RX, +1>(v, sm + lr * NX, 1, t, tw, RowSync<T>());
     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
     for (int s = 0; s < RX; ++s) {
-        const int i0 = t + T * slot_q<NX, RX, np>(s);
-        const long long f = fbase + i0;
+        const long long f = fbase + t + T * slot_q<NX, RX, np>(s);
         if (mode == INV_PLAIN) {
             if (valid) w[f] = v[s];
             s0 += (double)cabs2(v[s]);
             continue;
         }
-        const CT xv = x[f];
-        const CT b = born_B(M, rb, i0, adj != 0);
+        const CT b = bv[s];
         if (mode == INV_BORN) {
-            const CT del = cscale(cmul(b, csub(v[s], xv)), nu);
-            const CT xn = cadd(xv, del);
+            const CT del = cscale(cmul(b, csub(v[s], xv[s])), nu);
+            const CT xn = cadd(xv[s], del);
             if (valid) x[f] = xn;
             s0 += (double)cabs2(del);
             s1 += (double)cabs2(xn);
         } else {
             // v x = (1 - B) x
-            const CT vx = csub(xv, cmul(b, xv));
+            const CT vx = csub(xv[s], cmul(b, xv[s]));
             if (mode == INV_RESID) {
-                const CT yv = y[f];
-                const CT r = csub(yv, cadd(v[s], vx));
+                const CT r = csub(yv[s], cadd(v[s], vx));
                 if (valid) w[f] = r;
                 s0 += (double)cabs2(r);
-                s1 += (double)cabs2(yv);
+                s1 += (double)cabs2(yv[s]);
             } else {
                 const CT a = cadd(v[s], vx);
                 if (valid) w[f] = a;

@@ -26,7 +26,7 @@ using namespace cbs;
 
 namespace {
 
-constexpr int kHistCap = 8192;
+constexpr int kHostBuf = 8192;  // pinned host doubles
 constexpr int kSetupThreads = 256;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
@@ -280,23 +280,16 @@ __global__ void k_norm2(const double2* __restrict__ a, long long n, double* part
     block_sum2(s, 0.0, part + 2 * blockIdx.x);
 }
 
-// Fixed-order sum of nblk partial pairs -> out[0..1]; optionally appends
-// (out0, out1) to the history ring at *counter.
-__global__ void k_reduce(const double* __restrict__ part, int nblk, double* out, double* hist, int* counter, int cap)
+// Block b: fixed-order sum of the nblk partial pairs of slot b -> out[2b], out[2b+1].
+__global__ void k_reduce(const double* __restrict__ part, int nblk, double* out)
 {
+    const double* p = part + (long long)blockIdx.x * nblk * 2;
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-        a += part[2 * i];
-        b += part[2 * i + 1];
+        a += p[2 * i];
+        b += p[2 * i + 1];
     }
-    block_sum2(a, b, out);
-    if (hist != nullptr && threadIdx.x == 0) {
-        __threadfence_block();
-        const int k = *counter;
-        hist[2 * (k % cap)] = out[0];
-        hist[2 * (k % cap) + 1] = out[1];
-        *counter = k + 1;
-    }
+    block_sum2(a, b, out + 2 * blockIdx.x);
 }
 
 inline int grid_for(long long n, int threads = 256)
@@ -339,18 +332,17 @@ struct cbs_solver {
     float2 *x32 = nullptr, *y32 = nullptr, *w32 = nullptr;
     double* partials = nullptr;
     int npart = 0;
-    double* red = nullptr;      // [2] result of the last reduction
-    double* hist = nullptr;     // [kHistCap][2]
-    int* counter = nullptr;
-    double* host_red = nullptr; // pinned [2 * kHistCap]
+    int kslots = 1;             // iterations whose norm partials are kept between reductions
+    double* red = nullptr;      // [2] result of the last single reduction
+    double* hist = nullptr;     // [kslots][2] per-iteration (|dx|^2, |x|^2) of the last block
+    double* host_red = nullptr; // pinned [kHostBuf]
 
     Plan<double> P64{};
     Plan<float> P32{};
     cudaGraphExec_t graph64[2] = {nullptr, nullptr};
     cudaGraphExec_t graph32[2] = {nullptr, nullptr};
-    int graphK64[2] = {0, 0}, graphK32[2] = {0, 0};
     bool warmed64 = false, warmed32 = false;
-    int hist_pos = 0;  // host mirror of *counter
+    int hist_n = 0;          // entries of hist written by the last block
     long long launches = 0;  // kernels launched by the current call
 };
 
@@ -422,7 +414,6 @@ template <> struct Bufs<double> {
     static double2* y(cbs_solver* s) { return s->y64; }
     static double2* w(cbs_solver* s) { return s->w64; }
     static cudaGraphExec_t* graph(cbs_solver* s) { return s->graph64; }
-    static int* graphK(cbs_solver* s) { return s->graphK64; }
     static bool& warmed(cbs_solver* s) { return s->warmed64; }
 };
 template <> struct Bufs<float> {
@@ -431,71 +422,75 @@ template <> struct Bufs<float> {
     static float2* y(cbs_solver* s) { return s->y32; }
     static float2* w(cbs_solver* s) { return s->w32; }
     static cudaGraphExec_t* graph(cbs_solver* s) { return s->graph32; }
-    static int* graphK(cbs_solver* s) { return s->graphK32; }
     static bool& warmed(cbs_solver* s) { return s->warmed32; }
 };
 
-template <typename R> void reduce(cbs_solver* s, int nblk, bool record)
+// sum the partials of `nslots` slots into out[2 * slot]
+void reduce_slots(cbs_solver* s, int nblk, int nslots, double* out)
 {
-    k_reduce<<<1, 256, 0, s->st>>>(s->partials, nblk, s->red, record ? s->hist : nullptr, s->counter, kHistCap);
+    k_reduce<<<nslots, 256, 0, s->st>>>(s->partials, nblk, out);
     CUDA_TRY(cudaGetLastError());
-    if (record) s->hist_pos++;
+    s->launches += 1;
 }
 
-// one Born iteration on the precision-R buffers (eq. BornAlt)
-template <typename R> void iterate_once(cbs_solver* s, bool adj)
+// one Born iteration on the precision-R buffers (eq. BornAlt); its norm
+// partials go to slot `slot`
+template <typename R> void iterate_once(cbs_solver* s, bool adj, int slot)
 {
     Plan<R>& P = Bufs<R>::plan(s);
     auto x = Bufs<R>::x(s);
     auto y = Bufs<R>::y(s);
     auto w = Bufs<R>::w(s);
+    const int nblk = rows_blocks<R>(P);
     CUDA_TRY(launch_rows_fwd<R>(P, x, y, w, FWD_BORN, adj, s->st));
     if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, -1, s->st));
     CUDA_TRY(launch_last<R>(P, w, adj ? SYM_GREEN_ADJ : SYM_GREEN, s->st));
     if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, +1, s->st));
-    CUDA_TRY(launch_rows_inv<R>(P, x, y, w, INV_BORN, adj, (R)s->opt.nu, s->partials, s->st));
-    reduce<R>(s, rows_blocks<R>(P), true);
-    s->launches += (s->D == 3) ? 6 : 4;
+    CUDA_TRY(launch_rows_inv<R>(P, x, y, w, INV_BORN, adj, (R)s->opt.nu, s->partials + (size_t)slot * nblk * 2, s->st));
+    s->launches += (s->D == 3) ? 5 : 3;
 }
 
-// run n iterations, K at a time through a captured CUDA graph
+// n <= kslots iterations and one reduction of their norms into hist[0..n)
+template <typename R> void iterate_block(cbs_solver* s, int n, bool adj)
+{
+    for (int k = 0; k < n; ++k) iterate_once<R>(s, adj, k);
+    reduce_slots(s, rows_blocks<R>(Bufs<R>::plan(s)), n, s->hist);
+}
+
+// run n iterations in blocks of K = kslots; full blocks replay a captured CUDA graph
 template <typename R> void run_iterations(cbs_solver* s, int n, bool adj)
 {
-    const int K = s->opt.check_every;
+    const int K = s->kslots;
     bool& warmed = Bufs<R>::warmed(s);
     while (n > 0) {
-        if (!warmed || n < K) {
-            iterate_once<R>(s, adj);
+        const int blk = std::min(n, K);
+        if (!warmed || blk < K) {
+            iterate_block<R>(s, blk, adj);
             warmed = true;
-            --n;
-            continue;
-        }
-        cudaGraphExec_t& ge = Bufs<R>::graph(s)[adj ? 1 : 0];
-        int& gk = Bufs<R>::graphK(s)[adj ? 1 : 0];
-        if (ge == nullptr || gk != K) {
-            if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
-            cudaGraph_t g = nullptr;
-            CUDA_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-            const int pos0 = s->hist_pos;
-            try {
-                for (int k = 0; k < K; ++k) iterate_once<R>(s, adj);
-            } catch (...) {
-                cudaStreamEndCapture(s->st, &g);
-                if (g) cudaGraphDestroy(g);
-                throw;
+        } else {
+            cudaGraphExec_t& ge = Bufs<R>::graph(s)[adj ? 1 : 0];
+            if (ge == nullptr) {
+                cudaGraph_t g = nullptr;
+                const long long l0 = s->launches;
+                CUDA_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+                try {
+                    iterate_block<R>(s, K, adj);
+                } catch (...) {
+                    cudaStreamEndCapture(s->st, &g);
+                    if (g) cudaGraphDestroy(g);
+                    throw;
+                }
+                s->launches = l0;
+                CUDA_TRY(cudaStreamEndCapture(s->st, &g));
+                cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                CUDA_TRY(e);
             }
-            s->hist_pos = pos0;
-            s->launches -= (long long)K * ((s->D == 3) ? 6 : 4);
-            CUDA_TRY(cudaStreamEndCapture(s->st, &g));
-            cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
-            cudaGraphDestroy(g);
-            CUDA_TRY(e);
-            gk = K;
+            CUDA_TRY(cudaGraphLaunch(ge, s->st));
+            s->launches += (long long)K * ((s->D == 3) ? 5 : 3) + 1;
         }
-        CUDA_TRY(cudaGraphLaunch(ge, s->st));
-        s->hist_pos += K;
-        s->launches += (long long)K * ((s->D == 3) ? 6 : 4);
-        n -= K;
+        s->hist_n = blk;
+        n -= blk;
     }
 }
 
@@ -511,8 +506,8 @@ template <typename R> void apply_operator(cbs_solver* s, bool adj, int mode)
     CUDA_TRY(launch_last<R>(P, w, adj ? SYM_L_ADJ : SYM_L, s->st));
     if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, +1, s->st));
     CUDA_TRY(launch_rows_inv<R>(P, x, y, w, mode, adj, (R)0, s->partials, s->st));
-    reduce<R>(s, rows_blocks<R>(P), false);
-    s->launches += (s->D == 3) ? 6 : 4;
+    s->launches += (s->D == 3) ? 5 : 3;
+    reduce_slots(s, rows_blocks<R>(P), 1, s->red);
 }
 
 // w <- (L+I)^-1 x (or its adjoint)
@@ -538,10 +533,10 @@ void read_red(cbs_solver* s, double* out2)
     out2[1] = s->host_red[1];
 }
 
-// last history entry (|dx|^2, |x|^2) -> relative increment
+// last history entry (|dx|^2, |x|^2) of the last block -> relative increment
 double read_last_increment(cbs_solver* s)
 {
-    const int k = (s->hist_pos - 1) % kHistCap;
+    const int k = s->hist_n - 1;
     CUDA_TRY(cudaMemcpyAsync(s->host_red, s->hist + 2 * k, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     CUDA_TRY(cudaStreamSynchronize(s->st));
     return s->host_red[1] > 0 ? std::sqrt(s->host_red[0] / s->host_red[1]) : 0.0;
@@ -552,9 +547,8 @@ void norm2_64(cbs_solver* s, const double2* a, long long n, double* out)
     const int g = std::min(grid_for(n), s->npart);
     k_norm2<<<g, 256, 0, s->st>>>(a, n, s->partials);
     CUDA_TRY(cudaGetLastError());
-    k_reduce<<<1, 256, 0, s->st>>>(s->partials, g, s->red, nullptr, nullptr, kHistCap);
-    CUDA_TRY(cudaGetLastError());
-    s->launches += 2;
+    s->launches += 1;
+    reduce_slots(s, g, 1, s->red);
     double r[2];
     read_red(s, r);
     *out = r[0];
@@ -731,9 +725,7 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
     cbs_info info{};
     try {
         begin_call(s);
-        s->hist_pos = 0;
         s->launches = 0;
-        CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(int), s->st));
         CUDA_TRY(cudaEventRecord(s->ev0, s->st));
         prepare(s, src, x0, adj);
         cbs_status st;
@@ -878,7 +870,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         CUDA_TRY(cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreate(&s->ev0));
         CUDA_TRY(cudaEventCreate(&s->ev1));
-        CUDA_TRY(cudaMallocHost(&s->host_red, 2 * kHistCap * sizeof(double)));
+        CUDA_TRY(cudaMallocHost(&s->host_red, kHostBuf * sizeof(double)));
         TRACE("create: begin_call");
         begin_call(s);
         TRACE("create: tables");
@@ -1012,12 +1004,11 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         fill_plan<float>(s, s->P32);
         const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)), grid_for(n));
         s->npart = nb;
-        TRACE("create: partials %d", nb);
-        s->partials = dalloc<double>(s, (size_t)nb * 2);
+        s->kslots = std::min(o.check_every, kHostBuf / 2);
+        TRACE("create: partials %d x %d", nb, s->kslots);
+        s->partials = dalloc<double>(s, (size_t)nb * 2 * s->kslots);
         s->red = dalloc<double>(s, 2);
-        s->hist = dalloc<double>(s, (size_t)kHistCap * 2);
-        s->counter = dalloc<int>(s, 1);
-        CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(int), s->st));
+        s->hist = dalloc<double>(s, (size_t)s->kslots * 2);
         CUDA_TRY(cudaEventRecord(s->ev1, s->st));
         CUDA_TRY(cudaStreamSynchronize(s->st));
         float ms = 0;
@@ -1069,8 +1060,6 @@ cbs_status born_iterate(cbs_solver* s, const void* y, void* x, int n_iter, int a
     try {
         begin_call(s);
         const long long n = field_len(s);
-        s->hist_pos = 0;
-        CUDA_TRY(cudaMemsetAsync(s->counter, 0, sizeof(int), s->st));
         const bool f32 = s->opt.precision != CBS_FP64;
         if (f32) {
             k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)y, s->y32, 1.0, n);
@@ -1082,17 +1071,14 @@ cbs_status born_iterate(cbs_solver* s, const void* y, void* x, int n_iter, int a
         }
         int done = 0;
         while (done < n_iter) {
-            const int blk = std::min(kHistCap, n_iter - done);
-            for (int k = 0; k < blk; ++k) {
-                if (f32) iterate_once<float>(s, adjoint != 0);
-                else iterate_once<double>(s, adjoint != 0);
-            }
+            const int blk = std::min(s->kslots, n_iter - done);
+            if (f32) iterate_block<float>(s, blk, adjoint != 0);
+            else iterate_block<double>(s, blk, adjoint != 0);
             if (incr) {
-                CUDA_TRY(cudaMemcpyAsync(s->host_red, s->hist, 2 * kHistCap * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+                CUDA_TRY(cudaMemcpyAsync(s->host_red, s->hist, 2 * blk * sizeof(double), cudaMemcpyDeviceToHost, s->st));
                 CUDA_TRY(cudaStreamSynchronize(s->st));
                 for (int k = 0; k < blk; ++k) {
-                    const int j = (done + k) % kHistCap;
-                    const double a = s->host_red[2 * j], b = s->host_red[2 * j + 1];
+                    const double a = s->host_red[2 * k], b = s->host_red[2 * k + 1];
                     incr[done + k] = b > 0 ? std::sqrt(a / b) : 0.0;
                 }
             }
@@ -1196,9 +1182,9 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
     if (!s) return CBS_EINVAL;
     if (!y || !x || n_iter <= 0 || !ms || !nk) return set_err(s, CBS_EINVAL, "bad argument");
     const bool f32 = s->opt.precision != CBS_FP64;
-    const char* kn3[6] = {"rows_fwd", "axis_fwd", "last_symbol", "axis_inv", "rows_inv", "reduce"};
-    const char* kn2[4] = {"rows_fwd", "last_symbol", "rows_inv", "reduce"};
-    const int K = s->D == 3 ? 6 : 4;
+    const char* kn3[5] = {"rows_fwd", "axis_fwd", "last_symbol", "axis_inv", "rows_inv"};
+    const char* kn2[3] = {"rows_fwd", "last_symbol", "rows_inv"};
+    const int K = s->D == 3 ? 5 : 3;
     const char** kn = s->D == 3 ? kn3 : kn2;
     try {
         begin_call(s);
@@ -1224,7 +1210,6 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
                 CUDA_TRY(launch_last<float>(P, s->w32, SYM_GREEN, s->st)); mark();
                 if (s->D == 3) { CUDA_TRY(launch_axis<float>(P, s->w32, +1, s->st)); mark(); }
                 CUDA_TRY(launch_rows_inv<float>(P, s->x32, s->y32, s->w32, INV_BORN, 0, (float)s->opt.nu, s->partials, s->st)); mark();
-                reduce<float>(s, rows_blocks<float>(P), false); mark();
             } else {
                 Plan<double>& P = s->P64;
                 CUDA_TRY(launch_rows_fwd<double>(P, s->x64, s->y64, s->w64, FWD_BORN, 0, s->st)); mark();
@@ -1232,7 +1217,6 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
                 CUDA_TRY(launch_last<double>(P, s->w64, SYM_GREEN, s->st)); mark();
                 if (s->D == 3) { CUDA_TRY(launch_axis<double>(P, s->w64, +1, s->st)); mark(); }
                 CUDA_TRY(launch_rows_inv<double>(P, s->x64, s->y64, s->w64, INV_BORN, 0, s->opt.nu, s->partials, s->st)); mark();
-                reduce<double>(s, rows_blocks<double>(P), false); mark();
             }
             CUDA_TRY(cudaStreamSynchronize(s->st));
             for (int j = 0; j < K; ++j) {
