@@ -53,7 +53,7 @@ class cbs_info(ctypes.Structure):
 
 EXPORTS = ("solver_create", "solve_forward", "solve_adjoint", "residual_norm", "born_iterate", "green_apply",
            "operator_apply", "scale_source", "unscale_field", "solver_scalars", "solver_time_kernels",
-           "solver_destroy", "cbs_last_error")
+           "solver_destroy", "cbs_last_error", "green_apply_noalloc")
 
 _lock = threading.Lock()
 _lib = None
@@ -103,6 +103,8 @@ def load(path: str | None = None):
         lib.solver_destroy.argtypes = [V]
         lib.cbs_last_error.restype = ctypes.c_char_p
         lib.cbs_last_error.argtypes = [V]
+        lib.green_apply_noalloc.restype = S
+        lib.green_apply_noalloc.argtypes = [ctypes.POINTER(cbs_grid), D, ctypes.POINTER(D), V, V, I, V]
         if path is None:
             _lib = lib
         return lib

@@ -799,6 +799,11 @@ template <typename R> void fill_plan(cbs_solver* s, Plan<R>& P)
 
 }  // namespace
 
+namespace cbs {
+// lets other translation units of the library report through cbs_last_error(NULL)
+void set_create_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace cbs
+
 // ====================================================================== C ABI
 extern "C" {
 
