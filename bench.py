@@ -111,7 +111,7 @@ def cpu_oracle_rate(problem, n_iter=1):
                   problem.gamma_max)
     y = P.scale_source(problem.source)
     t0 = time.perf_counter()
-    P.iterate(y, n_iter=n_iter, nu=0.5)
+    P.iterate(y, n_iter=n_iter, nu=0.8)
     dt = time.perf_counter() - t0
     return problem.n_voxels * n_iter / dt, dt, O.max_threads()
 
@@ -172,7 +172,7 @@ def run_gpu(args):
     src = T(p.source, torch.complex128)
     field = torch.zeros((4,) + p.shape, dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    kw = dict(tol=TOL, check_every=args.check_every, tol_inner=args.tol_inner)
+    kw = dict(tol=TOL, check_every=args.check_every, tol_inner=args.tol_inner, nu=args.nu)
 
     def solve(precision):
         s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision=precision, **kw)
@@ -323,6 +323,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--check-every", type=int, default=50)
     ap.add_argument("--tol-inner", type=float, default=1e-4)
+    ap.add_argument("--nu", type=float, default=0.8)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels"])

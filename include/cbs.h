@@ -73,7 +73,7 @@ typedef struct {
 
 typedef struct {
     int precision;     /* CBS_FP64 (default), CBS_FP32_REFINE, CBS_FP32 */
-    double nu;         /* 0 < nu < 1 (eq. BornAlt); 0 -> 0.5 */
+    double nu;         /* 0 < nu < 1 (eq. BornAlt); 0 -> 0.8 */
     double beta;       /* 0 < beta < 1 (eq. C); 0 -> 0.95 */
     int shift_rule;    /* CBS_SHIFT_MIDRANGE (default) or CBS_SHIFT_MEDIAN */
     double tol;        /* relative scaled residual ||y - A_s x|| / ||y||; <= 0: run exactly max_iter */

@@ -127,7 +127,7 @@ def _check_field(t, shape):
 
 
 def solver_create(c0, rho, alpha, dx: float, omega: float, nabs, gamma_max: float, power: float = 2.0,
-                  precision="fp64", nu: float = 0.5, beta: float = 0.95, shift_rule: int = CBS_SHIFT_MIDRANGE,
+                  precision="fp64", nu: float = 0.8, beta: float = 0.95, shift_rule: int = CBS_SHIFT_MIDRANGE,
                   tol: float = 1e-6, tol_inner: float = 1e-4, max_iter: int = 100000, check_every: int = 50,
                   stream=None):
     """c0, rho, alpha: cuda float64 tensors of the grid shape (n[D-1], ..., n[0])."""

@@ -112,15 +112,19 @@ struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
-// Block-wide sum of two doubles; thread 0 writes them to out[0..1].
-__device__ __forceinline__ void block_sum2(double a, double b, double* out)
+// Block-wide sum of two values; thread 0 writes them to out[0..1].  Warps sum
+// in the accumulator type A (float32 for the float32 path: float64 arithmetic
+// is scarce on this GPU), the per-warp sums are combined in float64.
+template <typename A> __device__ __forceinline__ void block_sum2(A a_in, A b_in, double* out)
 {
     __shared__ double red[2][32];
+    A aa = a_in, bb = b_in;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
+        aa += __shfl_down_sync(0xffffffffu, aa, o);
+        bb += __shfl_down_sync(0xffffffffu, bb, o);
     }
+    double a = (double)aa, b = (double)bb;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) { red[0][w] = a; red[1][w] = b; }
     __syncthreads();
@@ -137,13 +141,17 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* out)
     }
 }
 
-// Rows of one block: 256 threads when the rows' shared memory fits in 32 KiB.
+// Rows of one block: 256 threads when the rows' shared memory fits in the
+// static limit (48 KiB less the reduction scratch).
 template <typename R, int NX, int RX> struct RowCfg {
     static constexpr int T = NX / RX;
     static constexpr int ROWS0 = (T >= 256) ? 1 : 256 / T;
-    static constexpr int CAP0 = 32768 / (NX * (int)sizeof(cplx<R>));
+    static constexpr int SL = sm_len<NX, true>();  // row length in shared memory (swizzled / skewed)
+    static constexpr int CAP0 = 47104 / (SL * (int)sizeof(cplx<R>));
     static constexpr int CAP = CAP0 < 1 ? 1 : CAP0;
-    static constexpr int ROWS = ROWS0 < CAP ? ROWS0 : CAP;
+    static constexpr int G = T < 32 ? 32 / T : 1;  // rows per warp: blocks are whole warps
+    static constexpr int ROWS1 = ((ROWS0 < CAP ? ROWS0 : CAP) / G) * G;
+    static constexpr int ROWS = ROWS1 < G ? G : ROWS1;
     static constexpr int THREADS = T * ROWS;
 };
 
@@ -151,14 +159,14 @@ template <typename R, int NX, int RX> struct RowCfg {
 // grid: ceil(C * N / n0 / ROWS); block: THREADS.  w[row] = FFT_x(B x + y) (FWD_BORN)
 // or FFT_x(x) (FWD_COPY).
 template <typename R, int NX, int RX>
-__global__ void __launch_bounds__(RowCfg<R, NX, RX>::THREADS)
+__global__ void __launch_bounds__(RowCfg<R, NX, RX>::THREADS, sizeof(R) == 4 ? 4 : 1)
 k_rows_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y,
            cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int mode, int adj)
 {
     using CT = cplx<R>;
     using Cfg = RowCfg<R, NX, RX>;
     constexpr int T = Cfg::T;
-    __shared__ CT sm[Cfg::ROWS * NX];
+    __shared__ CT sm[Cfg::ROWS * Cfg::SL];
     const int lr = threadIdx.x / T, t = threadIdx.x % T;
     const long long rows_per_comp = d.N / NX;
     const long long C = d.D + 1;
@@ -171,6 +179,8 @@ k_rows_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* __
     const long long vbase = rest * NX;
     const long long fbase = (long long)c * d.N + vbase;
     const RowB<R> rb = row_B(M, d.D, c, i1, i2, vbase);
+    TwCache<NX, RX, CT> tc;
+    tw_load<NX, RX, T>(tc, t, tw);
     CT v[RX];
 #pragma unroll
     for (int s = 0; s < RX; ++s) {
@@ -183,7 +193,7 @@ k_rows_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* __
             v[s] = xv;
         }
     }
-    fft_run<NX, RX, -1>(v, sm + lr * NX, 1, t, tw, RowSync<T>());
+    fft_run<NX, RX, -1, true>(v, sm + lr * Cfg::SL, 1, t, tw, tc, RowSync<T>());
     if (valid) {
         constexpr int np = plan_npass(NX, RX);
 #pragma unroll
@@ -196,16 +206,19 @@ k_rows_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* __
 // INV_RESID: z = IFFT_x(w) = L x;  r = y - z - v x;  w <- r;  partial (|r|^2, |y|^2)
 // INV_APPLY: z = IFFT_x(w) = L x;  w <- z + v x;           partial (|w|^2, 0)
 // INV_PLAIN: w <- IFFT_x(w);                               partial (|w|^2, 0)
-template <typename R, int NX, int RX>
-__global__ void __launch_bounds__(RowCfg<R, NX, RX>::THREADS)
+// BORN = true: the hot Born-update instance (mode must be INV_BORN); false:
+// the residual / apply / plain instance.
+template <typename R, int NX, int RX, bool BORN>
+__global__ void __launch_bounds__(RowCfg<R, NX, RX>::THREADS, (sizeof(R) == 4 && BORN) ? 3 : 1)
 k_rows_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y, cplx<R>* __restrict__ w,
-           const cplx<R>* __restrict__ tw, int mode, int adj, R nu, double* __restrict__ partials)
+           const cplx<R>* __restrict__ tw, int mode_in, int adj, R nu, double* __restrict__ partials)
 {
+    const int mode = BORN ? (int)INV_BORN : mode_in;
     using CT = cplx<R>;
     using Cfg = RowCfg<R, NX, RX>;
     constexpr int T = Cfg::T;
     constexpr int np = plan_npass(NX, RX);
-    __shared__ CT sm[Cfg::ROWS * NX];
+    __shared__ CT sm[Cfg::ROWS * Cfg::SL];
     const int lr = threadIdx.x / T, t = threadIdx.x % T;
     const long long rows_per_comp = d.N / NX;
     const long long C = d.D + 1;
@@ -218,29 +231,33 @@ k_rows_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restri
     const long long vbase = rest * NX;
     const long long fbase = (long long)c * d.N + vbase;
     const RowB<R> rb = row_B(M, d.D, c, i1, i2, vbase);
+    TwCache<NX, RX, CT> tc;
+    tw_load<NX, RX, T>(tc, t, tw);
     CT v[RX];
 #pragma unroll
     for (int s = 0; s < RX; ++s) v[s] = w[fbase + t + T * slot_q<NX, RX, 0>(s)];
     // issue the epilogue's loads (x, B, y at the output positions) before the
     // transform so their latency overlaps it
-    CT xv[RX], bv[RX], yv[RX];
+    CT xv[RX], bv[RX], yv[BORN ? 1 : RX];
     if (mode != INV_PLAIN) {
 #pragma unroll
         for (int s = 0; s < RX; ++s) {
             const int i0 = t + T * slot_q<NX, RX, np>(s);
             xv[s] = x[fbase + i0];
             bv[s] = born_B(M, rb, i0, adj != 0);
-            if (mode == INV_RESID) yv[s] = y[fbase + i0];
+            if constexpr (!BORN) {
+                if (mode == INV_RESID) yv[s] = y[fbase + i0];
+            }
         }
     }
-    fft_run<NX, RX, +1>(v, sm + lr * NX, 1, t, tw, RowSync<T>());
-    double s0 = 0.0, s1 = 0.0;
+    fft_run<NX, RX, +1, true>(v, sm + lr * Cfg::SL, 1, t, tw, tc, RowSync<T>());
+    R s0 = (R)0, s1 = (R)0;
 #pragma unroll
     for (int s = 0; s < RX; ++s) {
         const long long f = fbase + t + T * slot_q<NX, RX, np>(s);
         if (mode == INV_PLAIN) {
             if (valid) w[f] = v[s];
-            s0 += (double)cabs2(v[s]);
+            s0 += cabs2(v[s]);
             continue;
         }
         const CT b = bv[s];
@@ -248,24 +265,24 @@ k_rows_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restri
             const CT del = cscale(cmul(b, csub(v[s], xv[s])), nu);
             const CT xn = cadd(xv[s], del);
             if (valid) x[f] = xn;
-            s0 += (double)cabs2(del);
-            s1 += (double)cabs2(xn);
-        } else {
+            s0 += cabs2(del);
+            s1 += cabs2(xn);
+        } else if constexpr (!BORN) {
             // v x = (1 - B) x
             const CT vx = csub(xv[s], cmul(b, xv[s]));
             if (mode == INV_RESID) {
                 const CT r = csub(yv[s], cadd(v[s], vx));
                 if (valid) w[f] = r;
-                s0 += (double)cabs2(r);
-                s1 += (double)cabs2(yv[s]);
+                s0 += cabs2(r);
+                s1 += cabs2(yv[s]);
             } else {
                 const CT a = cadd(v[s], vx);
                 if (valid) w[f] = a;
-                s0 += (double)cabs2(a);
+                s0 += cabs2(a);
             }
         }
     }
-    if (!valid) { s0 = 0.0; s1 = 0.0; }
+    if (!valid) { s0 = (R)0; s1 = (R)0; }
     block_sum2(s0, s1, partials + 2 * (long long)blockIdx.x);
 }
 
@@ -292,10 +309,12 @@ k_axis_fft(Dims d, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw)
     const int i0 = xb * COLS + col;
     const bool valid = i0 < d.n0;
     const long long base = rest * (long long)d.n0 * d.n1 + (valid ? i0 : 0);
+    TwCache<NA, RA, CT> tc;
+    tw_load<NA, RA, T>(tc, t, tw);
     CT v[RA];
 #pragma unroll
     for (int s = 0; s < RA; ++s) v[s] = w[base + (long long)(t + T * slot_q<NA, RA, 0>(s)) * d.n0];
-    fft_run<NA, RA, S>(v, sm + col, COLS, t, tw, BlockSync());
+    fft_run<NA, RA, S>(v, sm + col, COLS, t, tw, tc, BlockSync());
     if (valid) {
         constexpr int np = plan_npass(NA, RA);
 #pragma unroll
@@ -350,7 +369,7 @@ __device__ __forceinline__ void apply_symbol(const Symbol<R>& Sy, int mode, cons
 }
 
 template <typename R, int NL, int RL, int COLS, int C>
-__global__ void __launch_bounds__((NL / RL) * COLS)
+__global__ void __launch_bounds__((NL / RL) * COLS, 2)
 k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int mode)
 {
     using CT = cplx<R>;

@@ -614,9 +614,12 @@ template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* 
         info->rel_residual = 0;
         return CBS_OK;
     }
+    // the float32 path iterates on y / ||y|| (and x / ||y||) so that squared
+    // magnitudes stay far from float32 underflow whatever the source scale
+    const double ys = std::sqrt(ny2);
     if (std::is_same<R, float>::value) {
-        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->y64, s->y32, 1.0, n);
-        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->x64, s->x32, 1.0, n);
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->y64, s->y32, 1.0 / ys, n);
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>(s->x64, s->x32, 1.0 / ys, n);
         CUDA_TRY(cudaGetLastError());
         s->launches += 2;
     }
@@ -645,7 +648,8 @@ template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* 
     }
     if (st == CBS_OK && tol > 0 && rel > tol) st = CBS_ENOCONV;
     if (std::is_same<R, float>::value) {
-        k_cast_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x32, s->x64, n);
+        CUDA_TRY(cudaMemsetAsync(s->x64, 0, n * sizeof(double2), s->st));
+        k_axpy_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x64, s->x32, ys, n);
         CUDA_TRY(cudaGetLastError());
         s->launches += 1;
     }
@@ -840,7 +844,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         return set_err(nullptr, CBS_EINVAL, "dx and omega must be positive");
     cbs_options o{};
     if (opt) o = *opt;
-    if (o.nu == 0) o.nu = 0.5;
+    if (o.nu == 0) o.nu = 0.8;
     if (o.beta == 0) o.beta = 0.95;
     if (o.tol_inner == 0) o.tol_inner = 1e-4;
     if (o.max_iter == 0) o.max_iter = 100000;

@@ -182,9 +182,52 @@ __device__ __forceinline__ void permute_slots(CT (&v)[R])
     for (int s = 0; s < R; ++s) v[s] = tmp[q_slot<N, R, PA>(slot_q<N, R, PB>(s))];
 }
 
+// Twiddles a thread needs over all passes: pass P with NS > 1 uses, for its
+// butterfly m and input k = 1..r-1, w^{(j mod NS) k N/(NS r)}.  When there are
+// few of them they are loaded into registers once per kernel (TwCache), else
+// read from the table at each pass.
+__host__ __device__ constexpr int tw_count_before(int N, int R, int P)
+{
+    int c = 0;
+    for (int p = 0; p < P; ++p) {
+        const int r = plan_radix(N, R, p);
+        if (plan_ns(N, R, p) > 1) c += (R / r) * (r - 1);
+    }
+    return c;
+}
+__host__ __device__ constexpr int tw_count(int N, int R) { return tw_count_before(N, R, plan_npass(N, R)); }
+template <int N, int R> struct TwPolicy {
+    static constexpr int count = tw_count(N, R);
+    static constexpr bool cached = count > 0 && count <= 16;
+    static constexpr int slots = cached ? count : 1;
+};
+
+template <int N, int R, typename CT> struct TwCache {
+    CT w[TwPolicy<N, R>::slots];
+};
+
+template <int N, int R, int T, int P = 0, typename CT>
+__device__ __forceinline__ void tw_load(TwCache<N, R, CT>& tc, int tid, const CT* __restrict__ tw)
+{
+    if constexpr (TwPolicy<N, R>::cached && P < plan_npass(N, R)) {
+        constexpr int r = plan_radix(N, R, P);
+        constexpr int NS = plan_ns(N, R, P);
+        if constexpr (NS > 1) {
+            constexpr int off = tw_count_before(N, R, P);
+#pragma unroll
+            for (int m = 0; m < R / r; ++m) {
+                const int jj = (tid + T * m) % NS;
+#pragma unroll
+                for (int k = 1; k < r; ++k) tc.w[off + m * (r - 1) + k - 1] = __ldg(&tw[jj * k * (N / (NS * r))]);
+            }
+        }
+        tw_load<N, R, T, P + 1>(tc, tid, tw);
+    }
+}
+
 // twiddle table: tw[m] = exp(-2 pi i m / N), m < N
-template <int N, int R, int T, int P, int S, typename CT>
-__device__ __forceinline__ void pass_compute(CT (&v)[R], int tid, const CT* __restrict__ tw)
+template <int N, int R, int T, int P, int S, bool USE_TC = true, typename CT>
+__device__ __forceinline__ void pass_compute(CT (&v)[R], int tid, const CT* __restrict__ tw, const TwCache<N, R, CT>& tc)
 {
     constexpr int r = plan_radix(N, R, P);
     constexpr int NS = plan_ns(N, R, P);
@@ -195,7 +238,9 @@ __device__ __forceinline__ void pass_compute(CT (&v)[R], int tid, const CT* __re
             const int jj = j % NS;
 #pragma unroll
             for (int k = 1; k < r; ++k) {
-                CT w = __ldg(&tw[jj * k * (N / (NS * r))]);
+                CT w;
+                if constexpr (USE_TC && TwPolicy<N, R>::cached) w = tc.w[tw_count_before(N, R, P) + m * (r - 1) + k - 1];
+                else w = __ldg(&tw[jj * k * (N / (NS * r))]);
                 v[m * r + k] = (S < 0) ? cmul(v[m * r + k], w) : cmulc(v[m * r + k], w);
             }
         }
@@ -203,10 +248,21 @@ __device__ __forceinline__ void pass_compute(CT (&v)[R], int tid, const CT* __re
     }
 }
 
-// Write the outputs of pass P to shared memory, then read the inputs of pass
-// P+1.  `sm` addresses element e at sm[e * ss].  The caller syncs (SYNC) so
-// that the previous reads finished before the writes.
-template <int N, int R, int T, int P, typename CT, typename Sync>
+// Shared-memory address of element e.  Column tiles (PAD = false): e * ss.
+// A row stored contiguously (PAD = true): a swizzle that keeps the Stockham
+// writes (stride r) and reads (stride N/r) of a 16-lane phase on distinct
+// banks: XOR of bits 3..6 into bits 0..3 when N >= 128, else a skew.
+template <int N> __host__ __device__ constexpr int row_swizzle(int e)
+{
+    return (N >= 128 && N % 16 == 0) ? (e ^ ((e >> 3) & 15)) : (N == 64 ? e + (e >> 3) + (e >> 6) : e + (e >> 4));
+}
+template <int N, bool PAD> __device__ __forceinline__ int sm_addr(int e, int ss) { return PAD ? row_swizzle<N>(e) : e * ss; }
+template <int N, bool PAD> __host__ __device__ constexpr int sm_len()
+{
+    return PAD ? ((N >= 128 && N % 16 == 0) ? N : row_swizzle<N>(N - 1) + 1) : N;
+}
+
+template <int N, int R, int T, int P, bool PAD, typename CT, typename Sync>
 __device__ __forceinline__ void pass_exchange(CT (&v)[R], CT* sm, int ss, int tid, Sync sync)
 {
     constexpr int r = plan_radix(N, R, P);
@@ -218,34 +274,37 @@ __device__ __forceinline__ void pass_exchange(CT (&v)[R], CT* sm, int ss, int ti
         const int j = tid + T * m;
         const int idx = (j / NS) * NS * r + (j % NS);
 #pragma unroll
-        for (int k = 0; k < r; ++k) sm[(idx + k * NS) * ss] = v[m * r + k];
+        for (int k = 0; k < r; ++k) sm[sm_addr<N, PAD>(idx + k * NS, ss)] = v[m * r + k];
     }
     sync();
 #pragma unroll
     for (int m = 0; m < R / rn; ++m) {
         const int j = tid + T * m;
 #pragma unroll
-        for (int k = 0; k < rn; ++k) v[m * rn + k] = sm[(j + k * (N / rn)) * ss];
+        for (int k = 0; k < rn; ++k) v[m * rn + k] = sm[sm_addr<N, PAD>(j + k * (N / rn), ss)];
     }
 }
 
 // Full transform.  On entry v[s] holds position tid + T*slot_q<N,R,0>(s); on
 // exit v[s] holds position tid + T*slot_q<N,R,npass>(s).
-template <int N, int R, int S, int P = 0, typename CT, typename Sync>
-__device__ __forceinline__ void fft_run(CT (&v)[R], CT* sm, int ss, int tid, const CT* __restrict__ tw, Sync sync)
+template <int N, int R, int S, bool PAD = false, int P = 0, typename CT, typename Sync>
+__device__ __forceinline__ void fft_run(CT (&v)[R], CT* sm, int ss, int tid, const CT* __restrict__ tw,
+                                        const TwCache<N, R, CT>& tc, Sync sync)
 {
     constexpr int T = N / R;
     constexpr int np = plan_npass(N, R);
     static_assert(np > 0, "unsupported FFT size / register split");
-    pass_compute<N, R, T, P, S>(v, tid, tw);
+    pass_compute<N, R, T, P, S>(v, tid, tw, tc);
     if constexpr (P + 1 < np) {
-        pass_exchange<N, R, T, P>(v, sm, ss, tid, sync);
-        fft_run<N, R, S, P + 1>(v, sm, ss, tid, tw, sync);
+        pass_exchange<N, R, T, P, PAD>(v, sm, ss, tid, sync);
+        fft_run<N, R, S, PAD, P + 1>(v, sm, ss, tid, tw, tc, sync);
     }
 }
 
 // Same for C independent transforms that share the thread mapping (used to
 // keep all components of a pencil in registers at once).
+// (twiddles read from the table: with C transforms in registers there is no
+// room to cache them)
 template <int N, int R, int C, int S, int P = 0, typename CT, typename Sync>
 __device__ __forceinline__ void fft_run_multi(CT (&v)[C][R], CT* sm, int ss, int cstride, int tid,
                                               const CT* __restrict__ tw, Sync sync)
@@ -253,8 +312,9 @@ __device__ __forceinline__ void fft_run_multi(CT (&v)[C][R], CT* sm, int ss, int
     constexpr int T = N / R;
     constexpr int np = plan_npass(N, R);
     static_assert(np > 0, "unsupported FFT size / register split");
+    const TwCache<N, R, CT> none{};
 #pragma unroll
-    for (int c = 0; c < C; ++c) pass_compute<N, R, T, P, S>(v[c], tid, tw);
+    for (int c = 0; c < C; ++c) pass_compute<N, R, T, P, S, false>(v[c], tid, tw, none);
     if constexpr (P + 1 < np) {
         constexpr int r = plan_radix(N, R, P);
         constexpr int NS = plan_ns(N, R, P);

@@ -78,7 +78,10 @@ template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x
     using Cfg = RowCfg<R, N, RX>;
     long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
     int grid = (int)((rows + Cfg::ROWS - 1) / Cfg::ROWS);
-    k_rows_inv<R, N, RX><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj, nu, partials);
+    if (mode == INV_BORN)
+        k_rows_inv<R, N, RX, true><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj, nu, partials);
+    else
+        k_rows_inv<R, N, RX, false><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj, nu, partials);
     return cudaGetLastError();
 }
 

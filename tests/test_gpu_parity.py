@@ -44,6 +44,7 @@ def make(shape, seed=1, n_abs=3, gamma_scale=0.5, precision="fp64", **kw):
     p = W.smooth_random_medium(shape, seed=seed, n_abs=n_abs)
     p.gamma_max = gamma_scale * p.omega
     cbs = _cbs()
+    kw.setdefault("nu", 0.5)
     s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max, precision=precision, **kw)
     P = O.Problem(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max)
     return p, s, P
@@ -261,7 +262,7 @@ def test_sphere_128_first_iterations_and_precisions():
     p = W.sphere_128()
     src = p.source
     s64 = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max, precision="fp64",
-                            tol=1e-6, check_every=50)
+                            tol=1e-6, check_every=50, nu=0.5)
     P = O.Problem(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max)
     y = P.scale_source(src)
     x = torch.zeros(s64.field_shape, dtype=torch.complex128, device=DEV)
