@@ -102,6 +102,21 @@ def _dist():
     return ws, rank
 
 
+def reduce_over_ranks(local_ms: float, local_units: float, device=None):
+    """Replica aggregation: (max step time over ranks, total units over ranks).  With one process
+    this is the identity; under torch.distributed (nccl on GPUs, gloo on CPU) it all-reduces."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms), float(local_units)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------------ oracle arm
 def cpu_oracle_rate(problem, n_iter=1):
     """Voxel-iterations/s of the FP64 CPU oracle on the host cores (bounded sample)."""
@@ -207,13 +222,8 @@ def run_gpu(args):
         infos.append(info)
     clk = clocks.stop()
     t_ms = np.array(times)
-    step_ms = float(t_ms.mean())
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
-    value = ws * Nv * float(np.mean(iters)) / (step_ms / 1e3)
+    step_ms, units = reduce_over_ranks(float(t_ms.mean()), Nv * float(np.mean(iters)), device=dev)
+    value = units / (step_ms / 1e3)
 
     # plain FP64 side by side (one warm-up, one timed)
     fp64 = None
