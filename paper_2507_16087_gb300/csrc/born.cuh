@@ -84,6 +84,21 @@ __device__ __forceinline__ RowB<R> row_B(const Medium<R>& M, int D, int c, int i
     return rb;
 }
 
+// B from the row's medium values already in registers (m0 = rs_c or kp, m1 = et)
+template <typename R>
+__device__ __forceinline__ cplx<R> born_B_vals(const Medium<R>& M, bool pres, R g, R m0, R m1, bool adj)
+{
+    R vr, vi;
+    if (!pres) {
+        vr = m0 * g - M.a1r;
+        vi = m0 * M.omega - M.a1i;
+    } else {
+        vr = m0 * (g + m1 * M.omega) - M.a2r;
+        vi = m0 * (M.omega - g * m1) - M.a2i;
+    }
+    return mk<cplx<R>, R>((R)1 - vr, adj ? vi : -vi);
+}
+
 template <typename R>
 __device__ __forceinline__ cplx<R> born_B(const Medium<R>& M, const RowB<R>& rb, int i0, bool adj)
 {
@@ -427,6 +442,209 @@ k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __re
             for (int s = 0; s < RL; ++s)
                 w[(long long)c * d.N + base + (long long)(t + T * slot_q<NL, RL, np>(s)) * astride] = v[c][s];
     }
+}
+
+// ------------------------------------------------- bulk (TMA) staged rows
+// cp.async.bulk copies of a block's contiguous rows into shared memory,
+// completed on an mbarrier.  Every wait is bounded: on timeout the kernel
+// records an error code in *err and leaves without touching its outputs.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr int kBulkWaitLimit = 1 << 22;  // try_wait rounds before a copy is declared lost
+constexpr int kErrBulkTimeout = 1;
+
+// true when the phase completed; false after kBulkWaitLimit rounds
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
+{
+    for (int i = 0; i < kBulkWaitLimit; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+template <typename R, int NX, int RX> struct BulkCfg {
+    using Rc = RowCfg<R, NX, RX>;
+    static constexpr int ROWS = Rc::ROWS;
+    static constexpr int T = Rc::T;
+    static constexpr int THREADS = Rc::THREADS;
+    static constexpr int ELEMS = ROWS * NX;
+    // field A (x or w), field B (y or x), medium m0, medium m1, two mbarriers
+    static constexpr size_t SMEM = 2 * (size_t)ELEMS * sizeof(cplx<R>) + 2 * (size_t)ELEMS * sizeof(R) + 16;
+    // the exchange reuses field A's rows in place; every copy is a multiple of 16 bytes
+    static constexpr bool OK = (Rc::SL == NX) && ((size_t)ELEMS * sizeof(R)) % 16 == 0;
+};
+
+// Born forward rows with bulk-staged x, y and medium (requires every block's
+// rows to lie in one component: rows_per_comp % ROWS == 0).
+template <typename R, int NX, int RX>
+__global__ void __launch_bounds__(BulkCfg<R, NX, RX>::THREADS, sizeof(R) == 4 ? 4 : 1)
+k_rows_fwd_bulk(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y,
+                cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int adj, int* err)
+{
+    using CT = cplx<R>;
+    using Cfg = BulkCfg<R, NX, RX>;
+    constexpr int T = Cfg::T;
+    constexpr int E = Cfg::ELEMS;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    CT* xs = reinterpret_cast<CT*>(smraw);
+    CT* ys = xs + E;
+    R* m0s = reinterpret_cast<R*>(ys + E);
+    R* m1s = m0s + E;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(m1s + E);
+    const int lr = threadIdx.x / T, t = threadIdx.x % T;
+    const long long rows_per_comp = d.N / NX;
+    const long long row0 = (long long)blockIdx.x * Cfg::ROWS;
+    const int c = (int)(row0 / rows_per_comp);
+    const long long rest0 = row0 % rows_per_comp;
+    const long long vbase0 = rest0 * NX;
+    const long long fbase0 = (long long)c * d.N + vbase0;
+    const bool pres = (c == d.D);
+    const R* m0g = (pres ? M.kp : (c == 0 ? M.rs[0] : (c == 1 ? M.rs[1] : M.rs[2]))) + vbase0;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t fb = E * sizeof(CT), mb = E * sizeof(R);
+        mbar_expect_tx(bar, 2 * fb + (pres ? 2 : 1) * mb);
+        bulk_g2s(xs, x + fbase0, fb, bar);
+        bulk_g2s(ys, y + fbase0, fb, bar);
+        bulk_g2s(m0s, m0g, mb, bar);
+        if (pres) bulk_g2s(m1s, M.et + vbase0, mb, bar);
+    }
+    // overlap: twiddles and row constants while the copies fly
+    TwCache<NX, RX, CT> tc;
+    tw_load<NX, RX, T>(tc, t, tw);
+    const long long rest = rest0 + lr;
+    const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
+    const RowB<R> rb = row_B(M, d.D, c, i1, i2, rest * NX);
+    if (!mbar_wait_bounded(bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(err, kErrBulkTimeout);
+        mbar_wait_bounded(bar, 0);
+        return;
+    }
+    CT v[RX];
+#pragma unroll
+    for (int s = 0; s < RX; ++s) {
+        const int i0 = t + T * slot_q<NX, RX, 0>(s);
+        const int e = lr * NX + i0;
+        const R g = __ldg(rb.g0 + i0) + rb.grest;
+        const CT b = born_B_vals(M, pres, g, m0s[e], pres ? m1s[e] : (R)0, adj != 0);
+        v[s] = cadd(cmul(b, xs[e]), ys[e]);
+    }
+    fft_run<NX, RX, -1, true>(v, xs + lr * NX, 1, t, tw, tc, RowSync<T>());
+    constexpr int np = plan_npass(NX, RX);
+    const long long fbase = fbase0 + (long long)lr * NX;
+#pragma unroll
+    for (int s = 0; s < RX; ++s) w[fbase + t + T * slot_q<NX, RX, np>(s)] = v[s];
+}
+
+// Born inverse rows with bulk-staged w (first barrier) and x + medium (second
+// barrier, needed only by the update after the transform).
+template <typename R, int NX, int RX>
+__global__ void __launch_bounds__(BulkCfg<R, NX, RX>::THREADS, sizeof(R) == 4 ? 4 : 1)
+k_rows_inv_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, cplx<R>* __restrict__ w,
+                const cplx<R>* __restrict__ tw, int adj, R nu, double* __restrict__ partials, int* err)
+{
+    using CT = cplx<R>;
+    using Cfg = BulkCfg<R, NX, RX>;
+    constexpr int T = Cfg::T;
+    constexpr int E = Cfg::ELEMS;
+    constexpr int np = plan_npass(NX, RX);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    CT* ws = reinterpret_cast<CT*>(smraw);
+    CT* xs = ws + E;
+    R* m0s = reinterpret_cast<R*>(xs + E);
+    R* m1s = m0s + E;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(m1s + E);
+    const int lr = threadIdx.x / T, t = threadIdx.x % T;
+    const long long rows_per_comp = d.N / NX;
+    const long long row0 = (long long)blockIdx.x * Cfg::ROWS;
+    const int c = (int)(row0 / rows_per_comp);
+    const long long rest0 = row0 % rows_per_comp;
+    const long long vbase0 = rest0 * NX;
+    const long long fbase0 = (long long)c * d.N + vbase0;
+    const bool pres = (c == d.D);
+    const R* m0g = (pres ? M.kp : (c == 0 ? M.rs[0] : (c == 1 ? M.rs[1] : M.rs[2]))) + vbase0;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t fb = E * sizeof(CT), mb = E * sizeof(R);
+        mbar_expect_tx(bar, fb);
+        bulk_g2s(ws, w + fbase0, fb, bar);
+        mbar_expect_tx(bar + 1, fb + (pres ? 2 : 1) * mb);
+        bulk_g2s(xs, x + fbase0, fb, bar + 1);
+        bulk_g2s(m0s, m0g, mb, bar + 1);
+        if (pres) bulk_g2s(m1s, M.et + vbase0, mb, bar + 1);
+    }
+    TwCache<NX, RX, CT> tc;
+    tw_load<NX, RX, T>(tc, t, tw);
+    const long long rest = rest0 + lr;
+    const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
+    const RowB<R> rb = row_B(M, d.D, c, i1, i2, rest * NX);
+    bool ok = mbar_wait_bounded(bar, 0);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, kErrBulkTimeout);
+        mbar_wait_bounded(bar + 1, 0);
+        return;
+    }
+    CT v[RX];
+#pragma unroll
+    for (int s = 0; s < RX; ++s) v[s] = ws[lr * NX + t + T * slot_q<NX, RX, 0>(s)];
+    fft_run<NX, RX, +1, true>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
+    ok = mbar_wait_bounded(bar + 1, 0);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, kErrBulkTimeout);
+        mbar_wait_bounded(bar + 1, 0);
+        return;
+    }
+    R s0 = (R)0, s1 = (R)0;
+    const long long fbase = fbase0 + (long long)lr * NX;
+#pragma unroll
+    for (int s = 0; s < RX; ++s) {
+        const int i0 = t + T * slot_q<NX, RX, np>(s);
+        const int e = lr * NX + i0;
+        const R g = __ldg(rb.g0 + i0) + rb.grest;
+        const CT b = born_B_vals(M, pres, g, m0s[e], pres ? m1s[e] : (R)0, adj != 0);
+        const CT xv = xs[e];
+        const CT del = cscale(cmul(b, csub(v[s], xv)), nu);
+        const CT xn = cadd(xv, del);
+        x[fbase + i0] = xn;
+        s0 += cabs2(del);
+        s1 += cabs2(xn);
+    }
+    block_sum2(s0, s1, partials + 2 * (long long)blockIdx.x);
 }
 
 }  // namespace cbs

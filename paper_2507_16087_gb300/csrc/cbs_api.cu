@@ -343,6 +343,7 @@ struct cbs_solver {
     cudaGraphExec_t graph32[2] = {nullptr, nullptr};
     bool warmed64 = false, warmed32 = false;
     int hist_n = 0;          // entries of hist written by the last block
+    int* errword = nullptr;  // device error word of the bulk-staged kernels
     long long launches = 0;  // kernels launched by the current call
 };
 
@@ -738,7 +739,14 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
         else st = solve_plain<double>(s, adj, &info);
         finish_field(s, field);
         CUDA_TRY(cudaEventRecord(s->ev1, s->st));
+        int herr = 0;
+        CUDA_TRY(cudaMemcpyAsync(&herr, s->errword, sizeof(int), cudaMemcpyDeviceToHost, s->st));
         CUDA_TRY(cudaStreamSynchronize(s->st));
+        if (herr != 0) {
+            CUDA_TRY(cudaMemsetAsync(s->errword, 0, sizeof(int), s->st));
+            CUDA_TRY(cudaStreamSynchronize(s->st));
+            st = CBS_ETIMEOUT;
+        }
         float ms = 0;
         CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
         info.t_solve_ms = ms;
@@ -751,6 +759,7 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
         if (info_out) *info_out = info;
         if (st == CBS_ENOCONV) s->err = "max_iter reached before tol";
         if (st == CBS_EDIVERGED) s->err = "iteration produced a non-finite value";
+        if (st == CBS_ETIMEOUT) s->err = "a bulk copy did not complete within its wait limit";
         return st;
     } catch (const CudaError& e) {
         return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
@@ -1018,6 +1027,10 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         s->partials = dalloc<double>(s, (size_t)nb * 2 * s->kslots);
         s->red = dalloc<double>(s, 2);
         s->hist = dalloc<double>(s, (size_t)s->kslots * 2);
+        s->errword = dalloc<int>(s, 1);
+        CUDA_TRY(cudaMemsetAsync(s->errword, 0, sizeof(int), s->st));
+        s->P64.err = s->errword;
+        s->P32.err = s->errword;
         CUDA_TRY(cudaEventRecord(s->ev1, s->st));
         CUDA_TRY(cudaStreamSynchronize(s->st));
         float ms = 0;

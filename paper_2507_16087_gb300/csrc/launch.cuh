@@ -44,7 +44,16 @@ template <typename R> struct Plan {
     Medium<R> M;
     Symbol<R> Sy;
     const cplx<R>* tw[3];  // twiddle table of each axis length
+    int* err = nullptr;    // device error word of the bulk-staged kernels (nullptr: plain kernels only)
 };
+
+// the Born row kernels stage their rows with bulk copies when every block's
+// rows lie in one component and the rows' exchange fits in place
+template <typename R, int N> inline bool bulk_rows_ok(const Plan<R>& P)
+{
+    using Cfg = BulkCfg<R, N, r_rows<R>(N)>;
+    return Cfg::OK && P.err != nullptr && (P.d.N / N) % Cfg::ROWS == 0;
+}
 
 template <typename R> inline int rows_blocks(const Plan<R>& P)
 {
@@ -67,6 +76,20 @@ template <typename R, int N> cudaError_t rows_fwd_n(const Plan<R>& P, const cplx
     using Cfg = RowCfg<R, N, RX>;
     long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
     int grid = (int)((rows + Cfg::ROWS - 1) / Cfg::ROWS);
+    if constexpr (BulkCfg<R, N, RX>::OK) {
+        if (mode == FWD_BORN && bulk_rows_ok<R, N>(P)) {
+            using B = BulkCfg<R, N, RX>;
+            auto kern = k_rows_fwd_bulk<R, N, RX>;
+            static bool attr = false;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            kern<<<grid, B::THREADS, B::SMEM, st>>>(P.d, P.M, x, y, w, P.tw[0], adj, P.err);
+            return cudaGetLastError();
+        }
+    }
     k_rows_fwd<R, N, RX><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj);
     return cudaGetLastError();
 }
@@ -78,6 +101,20 @@ template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x
     using Cfg = RowCfg<R, N, RX>;
     long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
     int grid = (int)((rows + Cfg::ROWS - 1) / Cfg::ROWS);
+    if constexpr (BulkCfg<R, N, RX>::OK) {
+        if (mode == INV_BORN && bulk_rows_ok<R, N>(P)) {
+            using B = BulkCfg<R, N, RX>;
+            auto kern = k_rows_inv_bulk<R, N, RX>;
+            static bool attr = false;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            kern<<<grid, B::THREADS, B::SMEM, st>>>(P.d, P.M, x, w, P.tw[0], adj, nu, partials, P.err);
+            return cudaGetLastError();
+        }
+    }
     if (mode == INV_BORN)
         k_rows_inv<R, N, RX, true><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj, nu, partials);
     else
