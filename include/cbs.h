@@ -153,6 +153,21 @@ cbs_status operator_apply(cbs_solver* s, const void* x, void* out, int adjoint);
 cbs_status scale_source(cbs_solver* s, const void* src, void* y, int adjoint);
 cbs_status unscale_field(cbs_solver* s, const void* x, void* field);
 
+/* Adjoint-state medium gradient (Sec. 2.3: the adjoint A^H lambda = g is
+ * solved by solve_adjoint).  Per voxel, in float64:
+ *   grad_c0  = Re conj(lambda_p) (db_p/dc0 - dq/dc0 p)
+ *   grad_rho = Re conj(lambda_p) (db_p/drho - dq/drho p)
+ *            + sum_eta 1/2 Re conj(lambda_eta) (s_u,eta - (S+ gamma_eta + i omega) u_eta)
+ *              at x and at x - e_eta (the staggered density, App. B.1)
+ * with q = (i omega + gamma)/(rho c^2), b_p = s_p/(rho c^2) (eq. HH1stOrderSH,
+ * eq. 118): i.e. dJ/dm for a misfit J with dJ = Re<g, dX>.  c0, rho, alpha:
+ * the device medium the solver was created from; src, field, adj_field: device
+ * complex128 [C][N] physical source, forward field and adjoint field;
+ * grad_c0, grad_rho: device float64 [N], overwritten (accumulate = 0) or added
+ * to (accumulate != 0). */
+cbs_status medium_gradient(cbs_solver* s, const double* c0, const double* rho, const double* alpha, const void* src,
+                           const void* field, const void* adj_field, double* grad_c0, double* grad_rho, int accumulate);
+
 /* Shifts and scaling: out[0..5] = Re a1, Im a1, Re a2, Im a2, lambda1, lambda2. */
 cbs_status solver_scalars(const cbs_solver* s, double* out);
 

@@ -53,7 +53,7 @@ class cbs_info(ctypes.Structure):
 
 EXPORTS = ("solver_create", "solve_forward", "solve_adjoint", "residual_norm", "born_iterate", "green_apply",
            "operator_apply", "scale_source", "unscale_field", "solver_scalars", "solver_time_kernels",
-           "solver_destroy", "cbs_last_error", "green_apply_noalloc")
+           "solver_destroy", "cbs_last_error", "green_apply_noalloc", "medium_gradient")
 
 _lock = threading.Lock()
 _lib = None
@@ -103,6 +103,8 @@ def load(path: str | None = None):
         lib.solver_destroy.argtypes = [V]
         lib.cbs_last_error.restype = ctypes.c_char_p
         lib.cbs_last_error.argtypes = [V]
+        lib.medium_gradient.restype = S
+        lib.medium_gradient.argtypes = [V, V, V, V, V, V, V, V, V, I]
         lib.green_apply_noalloc.restype = S
         lib.green_apply_noalloc.argtypes = [ctypes.POINTER(cbs_grid), D, ctypes.POINTER(D), V, V, I, V]
         if path is None:
@@ -255,6 +257,15 @@ class Solver:
         _check_field(x, self.field_shape)
         _check_field(field, self.field_shape)
         st = self._lib.unscale_field(self._h, _ptr(x), _ptr(field))
+        if st != CBS_OK:
+            self._raise(st)
+
+    def medium_gradient(self, c0, rho, alpha, src, field, adj_field, grad_c0, grad_rho, accumulate=False):
+        """Adjoint-state gradient contribution of one source (see include/cbs.h)."""
+        for t in (src, field, adj_field):
+            _check_field(t, self.field_shape)
+        st = self._lib.medium_gradient(self._h, _ptr(c0), _ptr(rho), _ptr(alpha), _ptr(src), _ptr(field),
+                                       _ptr(adj_field), _ptr(grad_c0), _ptr(grad_rho), int(accumulate))
         if st != CBS_OK:
             self._raise(st)
 

@@ -196,6 +196,67 @@ __global__ void k_setup_store(SetupIn s, double il1, double il2, double* rs64_0,
     }
 }
 
+// ---------------------------------------------------------------- gradient
+// Re <lambda, db/dm - (dA/dm) X> per voxel for m = c0 and m = rho (adjoint-state
+// gradient of a misfit; A^H lambda = g, Sec. 2.3).  A depends on the medium only
+// through its diagonal: q = (i omega + gamma) / (rho c^2) (eq. HH1stOrderSH,
+// eq. 118) and d_eta = (S+ rho)_eta (S+ gamma_eta + i omega) (App. B.1), whose
+// staggered density couples rho(x) to the velocity rows at x and x - e_eta.
+struct GradIn {
+    SetupIn m;
+    const double2* src;
+    const double2* X;
+    const double2* L;
+};
+
+__device__ __forceinline__ double re_conj_mul(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }  // Re(conj(a) b)
+
+__global__ void k_medium_gradient(GradIn g, double* __restrict__ grad_c, double* __restrict__ grad_r, int accumulate)
+{
+    const SetupIn& s = g.m;
+    const long long N = s.N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        int i0, i1, i2;
+        unravel(s, i, i0, i1, i2);
+        const double rho = s.rho[i], c0 = s.c0[i], al = s.alpha[i], w = s.omega;
+        const double gam = gamma_c(s, i0, i1, i2);
+        // fac = d/dc0 [(1 - 2 i alpha c0 / omega) / c0^2] = -2/c0^3 + 2 i alpha / (omega c0^2)
+        const double2 fac = make_double2(-2.0 / (c0 * c0 * c0), 2.0 * al / (w * c0 * c0));
+        // 1/(rho c^2) = (1 - 2 i alpha c0 / omega) / (rho c0^2)
+        const double k = 1.0 / (rho * c0 * c0);
+        const double2 ic2 = make_double2(k, -k * 2.0 * al * c0 / w);
+        const double2 iwg = make_double2(gam, w);  // i omega + gamma
+        const long long ip = (long long)s.D * N + i;
+        const double2 p = g.X[ip], lp = g.L[ip], sp = g.src[ip];
+        // c0: conj(lp) (sp fac - (i w + gam) fac p) / rho
+        const double2 dq = cmul(iwg, fac);
+        const double2 tc = csub(cmul(sp, fac), cmul(dq, p));
+        const double gc = re_conj_mul(lp, tc) / rho;
+        // rho: conj(lp) (-bp + q p) / rho with bp = sp / (rho c^2), q = (i w + gam) / (rho c^2)
+        const double2 bp = cmul(sp, ic2);
+        const double2 q = cmul(iwg, ic2);
+        double gr = re_conj_mul(lp, csub(cmul(q, p), bp)) / rho;
+        for (int e = 0; e < s.D; ++e) {
+            // staggered rows at x and at x - e_eta share rho(x) with weight 1/2
+            for (int side = 0; side < 2; ++side) {
+                int j0 = i0, j1 = i1, j2 = i2;
+                if (side == 1) {
+                    if (e == 0) j0 = (i0 + s.n0 - 1) % s.n0;
+                    else if (e == 1) j1 = (i1 + s.n1 - 1) % s.n1;
+                    else j2 = (i2 + s.n2 - 1) % s.n2;
+                }
+                const long long j = ((long long)j2 * s.n1 + j1) * s.n0 + j0;
+                const long long f = (long long)e * N + j;
+                const double gs = gamma_s(s, e, j0, j1, j2);
+                const double2 t = csub(g.src[f], cmul(make_double2(gs, w), g.X[f]));
+                gr += 0.5 * re_conj_mul(g.L[f], t);
+            }
+        }
+        grad_c[i] = (accumulate ? grad_c[i] : 0.0) + gc;
+        grad_r[i] = (accumulate ? grad_r[i] : 0.0) + gr;
+    }
+}
+
 // ---------------------------------------------------------------- field kernels
 struct ScaleIn {
     int D;
@@ -1183,6 +1244,30 @@ cbs_status unscale_field(cbs_solver* s, const void* x, void* field)
         const long long n = field_len(s);
         k_scale_blocks<<<grid_for(n), 256, 0, s->st>>>(s->D, s->N, 1.0 / std::sqrt(s->lam1), 1.0 / std::sqrt(s->lam2),
                                                        (const double2*)x, (double2*)field);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
+}
+
+cbs_status medium_gradient(cbs_solver* s, const double* c0, const double* rho, const double* alpha, const void* src,
+                           const void* field, const void* adj_field, double* grad_c0, double* grad_rho, int accumulate)
+{
+    if (!s) return CBS_EINVAL;
+    if (!c0 || !rho || !alpha || !src || !field || !adj_field || !grad_c0 || !grad_rho)
+        return set_err(s, CBS_EINVAL, "NULL argument");
+    try {
+        begin_call(s);
+        GradIn g;
+        g.m.D = s->D; g.m.n0 = s->n[0]; g.m.n1 = s->n[1]; g.m.n2 = s->n[2]; g.m.N = s->N; g.m.omega = s->omega;
+        g.m.c0 = c0; g.m.rho = rho; g.m.alpha = alpha;
+        for (int a = 0; a < 3; ++a) { g.m.gc[a] = s->gc64[a]; g.m.gs[a] = s->gs64[a]; }
+        g.src = (const double2*)src;
+        g.X = (const double2*)field;
+        g.L = (const double2*)adj_field;
+        k_medium_gradient<<<grid_for(s->N), 256, 0, s->st>>>(g, grad_c0, grad_rho, accumulate ? 1 : 0);
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaStreamSynchronize(s->st));
         return CBS_OK;

@@ -163,3 +163,64 @@ def random_source(shape, seed, velocity=True):
     if not velocity:
         s[:-1] = 0
     return s
+
+
+def layered_inversion(n=128, n_abs=20, seed=3, n_slabs=5, pert=0.03, sigma=4.0, ppw=6.0, f_hz=F0,
+                      src_grid=(4, 2), rec_grid=(8, 8), n_fd=20, fd_seed=33):
+    """Adjoint / gradient workload: 5 random-thickness slabs along z (c ~ U(1400, 3000), rho ~ U(900, 2000),
+    alpha = 0) plus a 3 % periodic-Gaussian-smoothed (sigma cells) random perturbation; point pressure sources
+    on a 4 x 2 grid and receivers on an 8 x 8 grid, all on the plane z = n_abs + 2.  Returns a dict with the
+    layered (data) medium, the perturbed medium, sources (S, 4, n, n, n), receiver index arrays and seeded
+    interior voxels for finite-difference checks."""
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    lo, hi = n_abs, n - n_abs
+    depth = hi - lo
+    min_thick = max(1, min(4, depth // n_slabs))  # 4 cells when the interior allows it
+    for _ in range(10000):
+        cuts = np.sort(rng.uniform(0, depth, n_slabs - 1))
+        edges = np.concatenate([[0.0], cuts, [float(depth)]]).round().astype(int)
+        if np.all(np.diff(edges) >= min_thick):
+            break
+    else:  # equal slabs
+        edges = np.linspace(0, depth, n_slabs + 1).round().astype(int)
+    c_s = rng.uniform(1400.0, 3000.0, n_slabs)
+    r_s = rng.uniform(900.0, 2000.0, n_slabs)
+    zc = np.clip(np.arange(n) - lo, 0, depth - 1)
+    slab = np.searchsorted(edges[1:], zc, side="right")
+    slab = np.clip(slab, 0, n_slabs - 1)
+    c_lay = np.broadcast_to(c_s[slab][:, None, None], shape).astype(np.float64).copy()
+    r_lay = np.broadcast_to(r_s[slab][:, None, None], shape).astype(np.float64).copy()
+
+    def smooth_noise():
+        a = rng.standard_normal(shape)
+        A = np.fft.fftn(a)
+        g = np.ones(shape)
+        for ax in range(3):
+            k = np.fft.fftfreq(n)
+            sh = [1, 1, 1]
+            sh[ax] = n
+            g = g * np.exp(-2.0 * (math.pi * k * sigma) ** 2).reshape(sh)
+        b = np.real(np.fft.ifftn(A * g))
+        return b / b.std()
+
+    c_pert = c_lay * (1.0 + pert * smooth_noise())
+    r_pert = r_lay * (1.0 + pert * smooth_noise())
+    dx = grid_step(ppw, f_hz)
+    z = n_abs + 2
+    sx = np.linspace(lo + 8, hi - 8, src_grid[0]).round().astype(int)
+    sy = np.linspace(lo + 8, hi - 8, src_grid[1]).round().astype(int)
+    srcs = []
+    for yy in sy:
+        for xx in sx:
+            srcs.append(point_source(shape, (int(xx), int(yy), z))[None])
+    sources = np.concatenate(srcs, axis=0)
+    rx = np.linspace(lo + 4, hi - 4, rec_grid[0]).round().astype(int)
+    ry = np.linspace(lo + 4, hi - 4, rec_grid[1]).round().astype(int)
+    RY, RX = np.meshgrid(ry, rx, indexing="ij")
+    rec = (np.full(RX.size, z), RY.ravel(), RX.ravel())  # numpy (z, y, x) order
+    frng = np.random.default_rng(fd_seed)
+    fd = frng.integers(lo + 2, hi - 2, size=(n_fd, 3))  # (z, y, x)
+    return dict(shape=shape, dx=dx, omega=2 * math.pi * f_hz, nabs=[[n_abs, n_abs]] * 3,
+                gamma_max=layer_gamma_max(n_abs, dx), c_layered=c_lay, rho_layered=r_lay, c0=c_pert, rho=r_pert,
+                alpha=np.zeros(shape), sources=sources, receivers=rec, fd_voxels=fd)
