@@ -280,6 +280,10 @@ def run_gpu(args):
     e2e = {"value": Nv * ie["iters"] / e2e_t[-1], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "time_to_1e-6_ms": 1e3 * e2e_t[-1]}
 
+    serving = None
+    if args.serve_sample > 0:
+        serving = serving_measure(args.serve_sample, seed=4, n_sat=min(16, args.serve_sample))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         rate, dt, cores = cpu_oracle_rate(p, 1)
@@ -295,7 +299,7 @@ def run_gpu(args):
                 "time_to_1e-6_ms": step_ms, "iters": float(np.mean(iters)),
                 "outer_iters": infos[-1]["outer_iters"], "rel_residual": infos[-1]["rel_residual"],
                 "setup_ms": infos[-1]["t_setup_ms"], "fp64": fp64, "roofline": roof, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "serving": serving}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -325,6 +329,71 @@ def run_kernels(args):
     return 0
 
 
+def serving_measure(n_requests, seed=4, n_sat=16, max_slots=6):
+    """Serving stream: first the saturated throughput from a burst of n_sat requests (all queued at once),
+    then n_requests Poisson arrivals at 0.8 x that rate; returns p50 / p99 latency and throughput."""
+    import torch
+
+    from paper_2507_16087_gb300 import serving as S
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    burst = S.make_requests(n=n_sat, seed=seed + 1000, device=dev)
+    S.Server(max_slots=max_slots).run(burst, realtime=False)
+    sat = S.summarize(burst)
+    rate = 0.8 * sat["throughput_req_s"]
+    reqs = S.make_requests(n=n_requests, seed=seed, rate=rate, device=dev)
+    srv = S.Server(max_slots=max_slots)
+    srv.run(reqs, realtime=True)
+    out = S.summarize(reqs)
+    out.update({"arrival_rate_req_s": rate, "saturated_req_s": sat["throughput_req_s"],
+                "max_concurrent": srv.max_concurrent, "max_slots": max_slots,
+                "grids": "64^3/96^3/128^3/192^3, 512^2/1024^2/2048^2; FP32+refine to 1e-6"})
+    return out
+
+
+def run_serve(args):
+    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests)
+    out["mode"] = "serve"
+    print(json.dumps(out))
+    return 0
+
+
+def run_skull(args):
+    """512^3 transcranial-like workload (shell + bowl, 24-cell layer): one FP32 + FP64-refinement solve to
+    a 1e-6 residual; prints one JSON line with iterations, time, voxel-iter/s, the float64 residual
+    recomputed through residual_norm, and per-kernel times."""
+    import torch
+
+    from paper_2507_16087_gb300 import cbs, workloads as W
+
+    t0 = time.perf_counter()
+    p = W.skull_shell(n=args.n)
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    c0, rho, al = T(p.c0), T(p.rho), T(p.alpha)
+    src = T(p.source)
+    del p.source
+    field = torch.zeros_like(src)
+    s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision="fp32_refine", tol=TOL,
+                          nu=args.nu, check_every=args.check_every)
+    info = s.solve_forward(src, field)
+    res = s.residual_norm(field, src)
+    y = torch.zeros_like(src)
+    s.scale_source(src, y)
+    x = torch.zeros_like(src)
+    kt = s.time_kernels(y, x, 3)
+    s.destroy()
+    Nv = int(np.prod(p.shape))
+    print(json.dumps({"mode": "skull", "n": args.n, "voxels": Nv, "iters": info["iters"],
+                      "outer_iters": info["outer_iters"], "rel_residual": info["rel_residual"],
+                      "residual_recomputed": res, "time_to_1e-6_ms": info["t_solve_ms"],
+                      "setup_ms": info["t_setup_ms"], "voxel_iters_per_s": Nv * info["iters"] / (info["t_solve_ms"] / 1e3),
+                      "kernel_ms": kt, "bowl_voxels": p.meta["bowl_voxels"], "generate_s": t_gen,
+                      "device_mem_gb": torch.cuda.max_memory_allocated() / 1e9}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,12 +405,20 @@ def main():
     ap.add_argument("--nu", type=float, default=0.8)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve"])
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--sat-requests", type=int, default=24)
+    ap.add_argument("--serve-sample", type=int, default=24)
+    ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.mode == "kernels":
         return run_kernels(args)
+    if args.mode == "skull":
+        return run_skull(args)
+    if args.mode == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -18,7 +18,8 @@
  *
  * Conventions shared by every entry point:
  *  - Grid: ndim = 2 or 3, extents n[0] (x, fastest), n[1] (y), n[2] (z);
- *    every extent is one of 8,12,16,24,32,48,64,96,128,192,256,512.
+ *    every extent is one of 8,12,16,24,32,48,64,96,128,192,256,512,1024,2048
+ *    (3D grids with an extent above 512 are accepted but need ~350 B/voxel).
  *  - Field / source arrays: caller-owned DEVICE buffers of (ndim+1)*N
  *    complex128 values (interleaved re, im; 16-byte aligned), component-major
  *    [u_x][u_y][(u_z)][p], each component laid out [n2][n1][n0].  Velocity

@@ -19,7 +19,7 @@ CBS_SHIFT_MIDRANGE, CBS_SHIFT_MEDIAN = 0, 1
 PRECISIONS = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE, "fp32": CBS_FP32}
 STATUS_NAMES = {0: "CBS_OK", 1: "CBS_EINVAL", 2: "CBS_ENOMEM", 3: "CBS_ECUDA", 4: "CBS_ENOCONV",
                 5: "CBS_EDIVERGED", 6: "CBS_ETIMEOUT"}
-SUPPORTED_SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512)
+SUPPORTED_SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 2048)
 
 
 class cbs_grid(ctypes.Structure):

@@ -18,14 +18,15 @@ template <typename R> __host__ __device__ constexpr int r_last(int n)
 }
 template <typename R> __host__ __device__ constexpr int cols_axis(int n)
 {
-    return sizeof(R) == 4 ? (n <= 256 ? 16 : 8) : (n <= 128 ? 8 : 4);
+    return sizeof(R) == 4 ? (n <= 256 ? 16 : (n <= 512 ? 8 : 4)) : (n <= 128 ? 8 : (n <= 512 ? 4 : 2));
 }
 template <typename R> __host__ __device__ constexpr int cols_last(int n)
 {
-    return sizeof(R) == 4 ? (n <= 128 ? 16 : (n <= 256 ? 8 : 4)) : (n <= 128 ? 8 : (n <= 256 ? 4 : 2));
+    return sizeof(R) == 4 ? (n <= 128 ? 16 : (n <= 256 ? 8 : (n <= 512 ? 4 : (n <= 1024 ? 4 : 2))))
+                          : (n <= 128 ? 8 : (n <= 256 ? 4 : (n <= 512 ? 2 : (n <= 1024 ? 2 : 1))));
 }
 
-#define CBS_FOR_EACH_SIZE(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512)
+#define CBS_FOR_EACH_SIZE(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024) X(2048)
 
 inline bool size_supported(long long n)
 {
@@ -80,12 +81,10 @@ template <typename R, int N> cudaError_t rows_fwd_n(const Plan<R>& P, const cplx
         if (mode == FWD_BORN && bulk_rows_ok<R, N>(P)) {
             using B = BulkCfg<R, N, RX>;
             auto kern = k_rows_fwd_bulk<R, N, RX>;
-            static bool attr = false;
-            if (!attr) {
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
-                if (e != cudaSuccess) return e;
-                attr = true;
-            }
+            // once per process, thread-safe (function-local static)
+            static const cudaError_t attr =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
+            if (attr != cudaSuccess) return attr;
             kern<<<grid, B::THREADS, B::SMEM, st>>>(P.d, P.M, x, y, w, P.tw[0], adj, P.err);
             return cudaGetLastError();
         }
@@ -105,12 +104,10 @@ template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x
         if (mode == INV_BORN && bulk_rows_ok<R, N>(P)) {
             using B = BulkCfg<R, N, RX>;
             auto kern = k_rows_inv_bulk<R, N, RX>;
-            static bool attr = false;
-            if (!attr) {
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
-                if (e != cudaSuccess) return e;
-                attr = true;
-            }
+            // once per process, thread-safe (function-local static)
+            static const cudaError_t attr =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
+            if (attr != cudaSuccess) return attr;
             kern<<<grid, B::THREADS, B::SMEM, st>>>(P.d, P.M, x, w, P.tw[0], adj, nu, partials, P.err);
             return cudaGetLastError();
         }
@@ -129,12 +126,8 @@ template <typename R, int N, int S> cudaError_t axis_n(const Plan<R>& P, cplx<R>
     constexpr int T = N / RA;
     const size_t smem = (size_t)N * COLS * sizeof(cplx<R>);
     auto kern = k_axis_fft<R, N, RA, COLS, S>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     int xblocks = (P.d.n0 + COLS - 1) / COLS;
     long long grid = (long long)(P.d.D + 1) * P.d.n2 * xblocks;
     kern<<<(unsigned)grid, T * COLS, smem, st>>>(P.d, w, P.tw[1]);
@@ -148,12 +141,8 @@ template <typename R, int N, int C> cudaError_t last_n(const Plan<R>& P, cplx<R>
     constexpr int T = N / RL;
     const size_t smem = (size_t)C * N * COLS * sizeof(cplx<R>);
     auto kern = k_last_symbol<R, N, RL, COLS, C>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     int xblocks = (P.d.n0 + COLS - 1) / COLS;
     long long grid = (long long)(C == 4 ? P.d.n1 : 1) * xblocks;
     kern<<<(unsigned)grid, T * COLS, smem, st>>>(P.d, P.Sy, w, P.tw[P.d.D - 1], mode);

@@ -224,3 +224,100 @@ def layered_inversion(n=128, n_abs=20, seed=3, n_slabs=5, pert=0.03, sigma=4.0, 
     return dict(shape=shape, dx=dx, omega=2 * math.pi * f_hz, nabs=[[n_abs, n_abs]] * 3,
                 gamma_max=layer_gamma_max(n_abs, dx), c_layered=c_lay, rho_layered=r_lay, c0=c_pert, rho=r_pert,
                 alpha=np.zeros(shape), sources=sources, receivers=rec, fd_voxels=fd)
+
+
+def _smooth_noise(shape, sigma, rng, dtype=np.float32):
+    """Unit-std white noise smoothed by a periodic Gaussian of width sigma cells (separable, per axis)."""
+    a = rng.standard_normal(shape).astype(dtype)
+    for ax, n in enumerate(shape):
+        k = np.fft.rfftfreq(n) if ax == len(shape) - 1 else np.fft.fftfreq(n)
+        g = np.exp(-2.0 * (math.pi * k * sigma) ** 2).astype(dtype)
+        sh = [1] * len(shape)
+        sh[ax] = g.size
+        if ax == len(shape) - 1:
+            a = np.fft.irfft(np.fft.rfft(a, axis=ax) * g.reshape(sh), n=n, axis=ax).astype(dtype)
+        else:
+            a = np.real(np.fft.ifft(np.fft.fft(a, axis=ax) * g.reshape(sh), axis=ax)).astype(dtype)
+    return a / a.std()
+
+
+def skull_shell(n=512, n_abs=24, seed=5, r_in=180.0, r_out=200.0, mod_amp=6.0, mod_sigma=8.0, var=0.02,
+                var_sigma=4.0, aperture=300.0, roc=300.0, ppw=6.0, f_hz=F0):
+    """Transcranial-like stand-in: a spherical shell (c 2800, rho 1850, 8 dB/cm/MHz) between radii r_in and
+    r_out (outer radius modulated by smoothed noise, |mod| <= mod_amp cells) in water, with a 2 % smoothed
+    variation of c and rho inside the shell; a focused bowl pressure source (spherical cap of radius of
+    curvature `roc`, aperture `aperture` cells, apex on the -x face at x = n_abs + 2, axis +x), uniform
+    amplitude on the cap voxels.  Synthetic: the paper's benchmark skull mesh is not available."""
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    c = (n - 1) / 2.0
+    ax = np.arange(n, dtype=np.float32) - c
+    z2 = (ax ** 2)[:, None, None]
+    y2 = (ax ** 2)[None, :, None]
+    x2 = (ax ** 2)[None, None, :]
+    r = np.sqrt(z2 + y2 + x2, dtype=np.float32)
+    mod = _smooth_noise(shape, mod_sigma, rng)
+    mod = np.clip(mod / max(float(np.abs(mod).max()), 1e-30) * mod_amp, -mod_amp, mod_amp)
+    shell = (r >= r_in) & (r < r_out + mod)
+    del mod
+    inner = r < r_in
+    del r
+    vc = _smooth_noise(shape, var_sigma, rng)
+    vr = _smooth_noise(shape, var_sigma, rng)
+    c0 = np.where(inner, C_WATER * (1.0 + var * vc), C_WATER).astype(np.float64)
+    rho = np.where(inner, RHO_WATER * (1.0 + var * vr), RHO_WATER).astype(np.float64)
+    del vc, vr
+    c0[shell] = 2800.0
+    rho[shell] = 1850.0
+    alpha = np.zeros(shape)
+    alpha[shell] = db_cm_mhz_to_np_m(8.0, f_hz)
+    del shell, inner
+    # bowl: voxels within half a cell of the sphere of radius roc centred at (apex + roc, c, c), lateral
+    # distance <= aperture / 2, on the apex side
+    x_apex = n_abs + 2
+    xs = np.arange(n, dtype=np.float64)
+    depth = roc - math.sqrt(roc ** 2 - (aperture / 2) ** 2)
+    xmax = int(math.ceil(x_apex + depth)) + 2
+    sub = np.zeros((n, n, xmax), dtype=bool)
+    lat2 = ((xs[:, None] - c) ** 2 + (xs[None, :] - c) ** 2)[:, :, None]
+    dist = np.sqrt(lat2 + (xs[None, None, :xmax] - (x_apex + roc)) ** 2)
+    sub[:] = (np.abs(dist - roc) < 0.5) & (lat2 <= (aperture / 2) ** 2) & (xs[None, None, :xmax] <= x_apex + roc)
+    src = np.zeros((4,) + shape, dtype=np.complex128)
+    src[3, :, :, :xmax][sub] = 1.0
+    dx = grid_step(ppw, f_hz)
+    return Problem(name=f"skull3d_{n}", c0=c0, rho=rho, alpha=alpha, dx=dx, omega=2 * math.pi * f_hz,
+                   nabs=[[n_abs, n_abs]] * 3, gamma_max=layer_gamma_max(n_abs, dx), source=src,
+                   meta=dict(bowl_voxels=int(sub.sum()), r_in=r_in, r_out=r_out))
+
+
+def smooth_random_medium_torch(shape, seed, c_range=(1400.0, 2800.0), rho_range=(900.0, 1900.0),
+                               alpha_db_range=(0.0, 5.0), sigma_frac=1.0 / 16, ppw=6.0, n_abs=16, f_hz=F0,
+                               device=None):
+    """The smooth_random_medium recipe generated on a torch device (seeded torch generator, torch.fft):
+    c0, rho, alpha are float64 device tensors.  Not bit-identical to the numpy version (other generator)."""
+    import torch
+
+    dev = torch.device("cuda", 0) if device is None else torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+
+    def smooth():
+        a = torch.rand(shape, generator=g, device=dev, dtype=torch.float64)
+        A = torch.fft.fftn(a)
+        for ax, n in enumerate(shape):
+            k = torch.fft.fftfreq(n, device=dev, dtype=torch.float64)
+            sh = [1] * len(shape)
+            sh[ax] = n
+            A = A * torch.exp(-2.0 * (math.pi * k * sigma_frac * n) ** 2).reshape(sh)
+        b = torch.fft.ifftn(A).real
+        lo, hi = b.min(), b.max()
+        return (b - lo) / torch.clamp(hi - lo, min=1e-300)
+
+    c0 = (c_range[0] + (c_range[1] - c_range[0]) * smooth()).contiguous()
+    rho = (rho_range[0] + (rho_range[1] - rho_range[0]) * smooth()).contiguous()
+    alpha = ((alpha_db_range[0] + (alpha_db_range[1] - alpha_db_range[0]) * smooth())
+             * db_cm_mhz_to_np_m(1.0, f_hz)).contiguous()
+    dx = grid_step(ppw, f_hz)
+    return Problem(name=f"random{len(shape)}d_dev", c0=c0, rho=rho, alpha=alpha, dx=dx, omega=2 * math.pi * f_hz,
+                   nabs=[[n_abs, n_abs] for _ in shape], gamma_max=layer_gamma_max(n_abs, dx) if n_abs > 0 else 0.0,
+                   meta=dict(seed=seed))
