@@ -159,6 +159,12 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- GPU arm
+# DRAM read + write bytes per launch of each float32 iteration kernel on the 128^3 workload, from one
+# `ncu --set full` capture of the current kernels (null the entry when its kernel changes)
+NCU_TRAFFIC_128 = {"rows_fwd": 217.21e6, "axis_fwd": 74.78e6, "last_symbol": 74.94e6, "axis_inv": 74.95e6,
+                   "rows_inv": 206.63e6}
+
+
 def kernel_bytes_per_voxel(D=3, fp=4):
     """Algorithmic bytes per voxel of each kernel of one iteration (reads + writes of fields and medium)."""
     C = D + 1
@@ -253,7 +259,8 @@ def run_gpu(args):
     achieved = bpv[top] * Nv / (kt[top] / 1e3) / 1e9
     iter_ms = sum(kt.values())
     roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC_128.get(top),
+            "algorithmic_bytes": bpv[top] * Nv,
             "bytes_per_voxel": bpv[top], "kernel_ms": kt,
             "iteration_ms": iter_ms,
             "iteration_frac": sum(bpv.values()) * Nv / (iter_ms / 1e3) / 1e9 / peak}

@@ -109,7 +109,8 @@ def sphere_field(points, centre, src, omega, a, c0, rho0, c1, rho1, alpha1, amp,
         so += A[m] * special.eval_legendre(m, co) * h2(m, k0 * ro)
         si += B[m] * special.eval_legendre(m, ci) * special.spherical_jn(m, k1 * ri)
     R = np.linalg.norm(points[~inside] - src, axis=-1)
-    out[~inside] = amp * np.exp(-1j * k0 * R) / (4 * np.pi * R) + so
+    with np.errstate(divide="ignore", invalid="ignore"):  # the source point itself is singular
+        out[~inside] = amp * np.exp(-1j * k0 * R) / (4 * np.pi * R) + so
     out[inside] = si
     return out
 
