@@ -405,6 +405,8 @@ struct cbs_solver {
     bool warmed64 = false, warmed32 = false;
     int hist_n = 0;          // entries of hist written by the last block
     int* errword = nullptr;  // device error word of the bulk-staged kernels
+    cudaAccessPolicyWindow l2_window{};
+    bool l2_window_set = false;
     long long launches = 0;  // kernels launched by the current call
 };
 
@@ -544,6 +546,20 @@ template <typename R> void run_iterations(cbs_solver* s, int n, bool adj)
                 }
                 s->launches = l0;
                 CUDA_TRY(cudaStreamEndCapture(s->st, &g));
+                if (s->l2_window_set) {
+                    size_t nn = 0;
+                    cudaGraphGetNodes(g, nullptr, &nn);
+                    std::vector<cudaGraphNode_t> nodes(nn);
+                    cudaGraphGetNodes(g, nodes.data(), &nn);
+                    cudaKernelNodeAttrValue kv{};
+                    kv.accessPolicyWindow = s->l2_window;
+                    for (auto nd : nodes) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                            cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributeAccessPolicyWindow, &kv);
+                    }
+                    cudaGetLastError();
+                }
                 cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
                 CUDA_TRY(e);
@@ -829,6 +845,36 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
     }
 }
 
+
+// Keep the float32 work array resident in L2 across the five kernels of an
+// iteration: an access-policy window marks it persisting (the others stream).
+// The persisting-L2 limit is a property of this process's CUDA context (it
+// ends with the context); it is raised only up to the device maximum.
+void set_l2_window(cbs_solver* s, void* base, size_t bytes)
+{
+    int dev = 0, max_persist = 0, max_window = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (max_persist <= 0 || max_window <= 0) return;
+    const size_t win = std::min(bytes, (size_t)max_window);
+    size_t cur = 0;
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (cur < std::min(win, (size_t)max_persist)) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(win, (size_t)max_persist));
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    cudaStreamAttrValue v{};
+    v.accessPolicyWindow.base_ptr = base;
+    v.accessPolicyWindow.num_bytes = win;
+    v.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)cur / (double)win);
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaStreamSetAttribute(s->st, cudaStreamAttributeAccessPolicyWindow, &v);
+    s->l2_window = v.accessPolicyWindow;
+    s->l2_window_set = true;
+    TRACE("L2 window %zu bytes, persisting limit %zu, hit ratio %f", win, cur, v.accessPolicyWindow.hitRatio);
+    cudaGetLastError();
+}
+
 template <typename R> void fill_plan(cbs_solver* s, Plan<R>& P)
 {
     P.d.D = s->D;
@@ -1077,6 +1123,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             s->x32 = dalloc<float2>(s, n);
             s->y32 = dalloc<float2>(s, n);
             s->w32 = dalloc<float2>(s, n);
+            if (std::getenv("CBS_NO_L2_WINDOW") == nullptr) set_l2_window(s, s->w32, (size_t)n * sizeof(float2));
         }
         TRACE("create: plans");
         fill_plan<double>(s, s->P64);
