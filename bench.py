@@ -161,8 +161,7 @@ def run_reference(args):
 # -------------------------------------------------------------------- GPU arm
 # DRAM read + write bytes per launch of each float32 iteration kernel on the 128^3 workload, from one
 # `ncu --set full` capture of the current kernels (null the entry when its kernel changes)
-NCU_TRAFFIC_128 = {"rows_fwd": 217.21e6, "axis_fwd": 74.78e6, "last_symbol": 74.94e6, "axis_inv": 74.95e6,
-                   "rows_inv": 206.63e6}
+NCU_TRAFFIC_128 = {"rows_fwd": 217.21e6, "last_symbol": 74.94e6, "rows_inv": 206.63e6}
 
 
 def kernel_bytes_per_voxel(D=3, fp=4):

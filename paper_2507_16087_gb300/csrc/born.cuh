@@ -160,7 +160,8 @@ template <typename A> __device__ __forceinline__ void block_sum2(A a_in, A b_in,
 // static limit (48 KiB less the reduction scratch).
 template <typename R, int NX, int RX> struct RowCfg {
     static constexpr int T = NX / RX;
-    static constexpr int ROWS0 = (T >= 256) ? 1 : 256 / T;
+    // 256 threads (8 or 12 values each), or 2048 values per block with 16 values per thread
+    static constexpr int ROWS0 = (T >= 256) ? 1 : (RX >= 16 ? (2048 / NX < 1 ? 1 : 2048 / NX) : 256 / T);
     static constexpr int SL = sm_len<NX, true>();  // row length in shared memory (swizzled / skewed)
     static constexpr int CAP0 = 47104 / (SL * (int)sizeof(cplx<R>));
     static constexpr int CAP = CAP0 < 1 ? 1 : CAP0;

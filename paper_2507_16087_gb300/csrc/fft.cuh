@@ -2,7 +2,7 @@
 //
 // A length-N transform is done by T = N/R threads, each holding R complex
 // values in registers.  The transform is a sequence of radix-r passes (r in
-// {2,3,4,8}, r | R) in Stockham autosort order: pass p with sub-transform size
+// {2,3,4,8,16}, r | R) in Stockham autosort order: pass p with sub-transform size
 // Ns takes, for butterfly j, the inputs j + k N/r, multiplies input k by
 // w^{(j mod Ns) k N/(Ns r)} (w = exp(-2 pi i / N)), runs an r-point DFT and
 // writes output k to (j div Ns) Ns r + (j mod Ns) + k Ns.  Between passes the
@@ -26,47 +26,47 @@ template <> struct real_of<float2> { using T = float; };
 template <> struct real_of<double2> { using T = double; };
 
 template <typename CT, typename R> __host__ __device__ __forceinline__ CT mk(R a, R b) { CT c; c.x = a; c.y = b; return c; }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 // a * conj(b)
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b)
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b)
 {
     return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 // multiply by s*i  (s = +1 or -1)
-template <int S> __device__ __forceinline__ float2 mul_si(float2 a) { return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
-template <int S> __device__ __forceinline__ double2 mul_si(double2 a) { return S > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x); }
-__device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+template <int S> __host__ __device__ __forceinline__ float2 mul_si(float2 a) { return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+template <int S> __host__ __device__ __forceinline__ double2 mul_si(double2 a) { return S > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
 // --------------------------------------------------------------- r-point DFTs
 // X_q = sum_m x_m exp(S 2 pi i m q / r), S = -1 forward, +1 inverse.
-template <int S, typename CT> __device__ __forceinline__ void dft2(CT* v)
+template <int S, typename CT> __host__ __device__ __forceinline__ void dft2(CT* v)
 {
     CT a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
 }
 
-template <int S, typename CT> __device__ __forceinline__ void dft4(CT* v)
+template <int S, typename CT> __host__ __device__ __forceinline__ void dft4(CT* v)
 {
     CT s0 = cadd(v[0], v[2]), d0 = csub(v[0], v[2]);
     CT s1 = cadd(v[1], v[3]), d1 = mul_si<S>(csub(v[1], v[3]));
@@ -76,7 +76,7 @@ template <int S, typename CT> __device__ __forceinline__ void dft4(CT* v)
     v[3] = csub(d0, d1);
 }
 
-template <int S, typename CT> __device__ __forceinline__ void dft3(CT* v)
+template <int S, typename CT> __host__ __device__ __forceinline__ void dft3(CT* v)
 {
     using R = typename real_of<CT>::T;
     const R h = (R)0.86602540378443864676372317075294;  // sin(2 pi / 3)
@@ -91,7 +91,7 @@ template <int S, typename CT> __device__ __forceinline__ void dft3(CT* v)
 }
 
 // 8 = 2 x 4: even/odd 4-point DFTs combined with w8^q = exp(S 2 pi i q / 8)
-template <int S, typename CT> __device__ __forceinline__ void dft8(CT* v)
+template <int S, typename CT> __host__ __device__ __forceinline__ void dft8(CT* v)
 {
     using R = typename real_of<CT>::T;
     const R c = (R)0.70710678118654752440084436210485;
@@ -113,12 +113,52 @@ template <int S, typename CT> __device__ __forceinline__ void dft8(CT* v)
     v[7] = csub(e[3], o3);
 }
 
-template <int r, int S, typename CT> __device__ __forceinline__ void dft(CT* v)
+// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; inner 4-point DFTs over n1, twiddles
+// w16^{n2 k1}, outer 4-point DFTs over n2 (w16 = exp(S 2 pi i / 16))
+template <int S, typename CT> __host__ __device__ __forceinline__ void dft16(CT* v)
+{
+    using R = typename real_of<CT>::T;
+    const R c1 = (R)0.92387953251128675612818318939679;  // cos(pi/8)
+    const R s1 = (R)0.38268343236508977172845998403040;  // sin(pi/8)
+    const R h = (R)0.70710678118654752440084436210485;
+    CT a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        CT t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+        dft4<S>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
+    }
+    const CT w1 = mk<CT, R>(c1, (R)S * s1);
+    const CT w2 = mk<CT, R>(h, (R)S * h);
+    const CT w3 = mk<CT, R>(s1, (R)S * c1);
+    const CT w6 = mk<CT, R>(-h, (R)S * h);
+    const CT w9 = mk<CT, R>(-c1, -(R)S * s1);
+    a[1][1] = cmul(a[1][1], w1);
+    a[1][2] = cmul(a[1][2], w2);
+    a[1][3] = cmul(a[1][3], w3);
+    a[2][1] = cmul(a[2][1], w2);
+    a[2][2] = mul_si<S>(a[2][2]);
+    a[2][3] = cmul(a[2][3], w6);
+    a[3][1] = cmul(a[3][1], w3);
+    a[3][2] = cmul(a[3][2], w6);
+    a[3][3] = cmul(a[3][3], w9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        CT t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+        dft4<S>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
+template <int r, int S, typename CT> __host__ __device__ __forceinline__ void dft(CT* v)
 {
     if constexpr (r == 2) dft2<S>(v);
     else if constexpr (r == 3) dft3<S>(v);
     else if constexpr (r == 4) dft4<S>(v);
     else if constexpr (r == 8) dft8<S>(v);
+    else if constexpr (r == 16) dft16<S>(v);
 }
 
 // ------------------------------------------------------------------- plans
@@ -126,6 +166,7 @@ template <int r, int S, typename CT> __device__ __forceinline__ void dft(CT* v)
 __host__ __device__ constexpr int plan_step(int rem, int R)
 {
     return (rem % 3 == 0 && R % 3 == 0) ? 3
+         : (rem % 16 == 0 && R % 16 == 0) ? 16
          : (rem % 8 == 0 && R % 8 == 0) ? 8
          : (rem % 4 == 0 && R % 4 == 0) ? 4
          : (rem % 2 == 0 && R % 2 == 0) ? 2 : 0;

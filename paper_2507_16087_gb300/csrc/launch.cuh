@@ -12,13 +12,18 @@ namespace cbs {
 // Elements per thread of one transform (RX for row/axis kernels, RL for the
 // all-components pencil kernel, which keeps C transforms in registers).
 template <typename R> __host__ __device__ constexpr int r_rows(int n) { return (n % 3 == 0) ? 12 : 8; }
+// strided-axis transforms: 16 values per thread for float32 128 / 256 (two passes, radix 16 then 8 or 16)
+template <typename R> __host__ __device__ constexpr int r_axis(int n)
+{
+    return (n % 3 == 0) ? 12 : ((sizeof(R) == 4 && (n == 128 || n == 256)) ? 16 : 8);
+}
 template <typename R> __host__ __device__ constexpr int r_last(int n)
 {
     return sizeof(R) == 4 ? ((n % 3 == 0) ? 6 : 8) : ((n % 3 == 0) ? 6 : 4);
 }
 template <typename R> __host__ __device__ constexpr int cols_axis(int n)
 {
-    return sizeof(R) == 4 ? (n <= 256 ? 16 : (n <= 512 ? 8 : 4)) : (n <= 128 ? 8 : (n <= 512 ? 4 : 2));
+    return sizeof(R) == 4 ? (n == 128 ? 32 : (n <= 256 ? 16 : (n <= 512 ? 8 : 4))) : (n <= 128 ? 8 : (n <= 512 ? 4 : 2));
 }
 template <typename R> __host__ __device__ constexpr int cols_last(int n)
 {
@@ -121,7 +126,7 @@ template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x
 
 template <typename R, int N, int S> cudaError_t axis_n(const Plan<R>& P, cplx<R>* w, cudaStream_t st)
 {
-    constexpr int RA = r_rows<R>(N);
+    constexpr int RA = r_axis<R>(N);
     constexpr int COLS = cols_axis<R>(N);
     constexpr int T = N / RA;
     const size_t smem = (size_t)N * COLS * sizeof(cplx<R>);

@@ -82,7 +82,8 @@ def test_green_apply_fp64(shape, adjoint):
     assert rel(out.cpu().numpy(), ref) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(24, 32), (96, 64), (16, 24, 12), (64, 64, 64)])
+@pytest.mark.parametrize("shape", [(24, 32), (96, 64), (16, 24, 12), (64, 64, 64), (128, 256), (24, 128, 128),
+                                   (16, 256, 128)])
 def test_green_apply_fp32(shape):
     _, s, P = make(shape, seed=8, precision="fp32")
     v = W.random_source(shape, 9)
@@ -113,8 +114,8 @@ def test_born_iterations_fp64(shape, adjoint):
     assert np.allclose(inc, incr, rtol=1e-9, atol=0)
 
 
-def test_born_iterations_fp32():
-    shape = (16, 24, 32)
+@pytest.mark.parametrize("shape", [(16, 24, 32), (24, 128, 128), (256, 128)])
+def test_born_iterations_fp32(shape):
     _, s, P = make(shape, seed=14, precision="fp32")
     y = P.scale_source(W.random_source(shape, 15))
     x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
