@@ -364,6 +364,39 @@ def run_serve(args):
     return 0
 
 
+def run_sweep(args):
+    """Convergence versus contrast (a central disc in c or in rho, line source): FP32 + refinement
+    iterations to a 1e-6 residual for each contrast; one JSON line."""
+    import torch
+
+    from paper_2507_16087_gb300 import cbs, workloads as W
+
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rows = []
+    cases = [("c", d) for d in (0.0, 250.0, 500.0, 1000.0, 2000.0)] + [("rho", d) for d in (500.0, 1000.0, 2000.0, 4000.0)]
+    for kind, d in cases:
+        p = W.disc_perturbation(n=256, dc=d if kind == "c" else 0.0, drho=d if kind == "rho" else 0.0)
+        for rule in (cbs.CBS_SHIFT_MIDRANGE, cbs.CBS_SHIFT_MEC):
+            s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max,
+                                  precision="fp32_refine", tol=TOL, shift_rule=rule, max_iter=200000)
+            field = torch.zeros((3,) + p.shape, dtype=torch.complex128, device=dev)
+            info = s.solve_forward(T(p.source), field, allow_noconv=True)
+            s.destroy()
+            rows.append({"kind": kind, "delta": d, "shift": "mec" if rule else "midrange", "iters": info["iters"],
+                         "rel_residual": info["rel_residual"], "ms": info["t_solve_ms"]})
+    e1 = W.three_discs()
+    s = cbs.solver_create(T(e1.c0), T(e1.rho), T(e1.alpha), e1.dx, e1.omega, e1.nabs, e1.gamma_max,
+                          precision="fp32_refine", tol=TOL, max_iter=400000)
+    field = torch.zeros((3,) + e1.shape, dtype=torch.complex128, device=dev)
+    i1 = s.solve_forward(T(e1.source), field, allow_noconv=True)
+    s.destroy()
+    print(json.dumps({"mode": "sweep", "grid": "256^2, 6 PPW, 16-cell layer, disc r=32, line source", "rows": rows,
+                      "three_discs": {"iters": i1["iters"], "rel_residual": i1["rel_residual"],
+                                      "ms": i1["t_solve_ms"], "status": i1["status"]}}))
+    return 0
+
+
 def run_skull(args):
     """512^3 transcranial-like workload (shell + bowl, 24-cell layer): one FP32 + FP64-refinement solve to
     a 1e-6 residual; prints one JSON line with iterations, time, voxel-iter/s, the float64 residual
@@ -411,7 +444,7 @@ def main():
     ap.add_argument("--nu", type=float, default=0.8)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve", "sweep"])
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--sat-requests", type=int, default=24)
     ap.add_argument("--serve-sample", type=int, default=24)
@@ -425,6 +458,8 @@ def main():
         return run_skull(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

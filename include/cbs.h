@@ -54,7 +54,7 @@ typedef enum {
 } cbs_status;
 
 enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1, CBS_FP32 = 2 };
-enum { CBS_SHIFT_MIDRANGE = 0, CBS_SHIFT_MEDIAN = 1 };
+enum { CBS_SHIFT_MIDRANGE = 0, CBS_SHIFT_MEDIAN = 1, CBS_SHIFT_MEC = 2 };
 
 typedef struct {
     int ndim;      /* 2 or 3 */
@@ -76,7 +76,9 @@ typedef struct {
     int precision;     /* CBS_FP64 (default), CBS_FP32_REFINE, CBS_FP32 */
     double nu;         /* 0 < nu < 1 (eq. BornAlt); 0 -> 0.8 */
     double beta;       /* 0 < beta < 1 (eq. C); 0 -> 0.95 */
-    int shift_rule;    /* CBS_SHIFT_MIDRANGE (default) or CBS_SHIFT_MEDIAN */
+    int shift_rule;    /* CBS_SHIFT_MIDRANGE (default), CBS_SHIFT_MEDIAN, or CBS_SHIFT_MEC: centre of
+                          the minimum enclosing circle of the support points of the value set in
+                          64 directions (Sec. 4's recommendation, to within the polygon's sag) */
     double tol;        /* relative scaled residual ||y - A_s x|| / ||y||; <= 0: run exactly max_iter */
     double tol_inner;  /* FP32_REFINE: inner relative reduction per outer step; 0 -> 1e-4 */
     int max_iter;      /* Born iterations (all inner iterations for FP32_REFINE); 0 -> 100000 */
@@ -102,7 +104,7 @@ typedef struct cbs_solver cbs_solver;
 /* Build a solver for one medium, frequency and grid (Algorithm 1
  * preprocessing): complex sound speed (eq. 118), staggered density
  * (App. B.1), diagonal values, shifts a1, a2 (midrange of the diagonal values
- * by default; componentwise median on request), lambda_j = max|diag - a_j| /
+ * by default; componentwise median or minimum enclosing circle on request), lambda_j = max|diag - a_j| /
  * beta (eq. C; lambda_j = |a_j| when that max is 0), per-axis wavenumber and
  * twiddle tables.  c0, rho, alpha: device float64 [N].  Rejects (CBS_EINVAL)
  * non-finite values, c0 <= 0, rho <= 0, alpha < 0, unsupported extents,

@@ -31,7 +31,8 @@
  *    staggered values evaluated at xi + 1/2 (Sec. 2.1 names gamma but gives no
  *    profile; App. B.1 says gamma is evaluated analytically at staggered points).
  *  - shifts a1, a2: midrange (bounding-box centre) of the diagonal values by
- *    default; componentwise median is the Algorithm 1 example (rule 1).
+ *    default; componentwise median is the Algorithm 1 example (rule 1); the
+ *    centre of the minimum enclosing circle, recommended in Sec. 4 (rule 2).
  *  - lambda_j = max|diag_j - a_j| / beta (eq. C); if that max is 0, lambda_j =
  *    |a_j| (and setup fails if a_j is 0 too).
  *  - pressure row divided by rho c^2 with the complex c^2 of eq. 118 (eq.
@@ -229,10 +230,65 @@ static double median_of(double* v, long m)
     return (m % 2) ? v[m / 2] : 0.5 * (v[m / 2 - 1] + v[m / 2]);
 }
 
+/* circle through three points (NULL-safe for collinear input: returns 0) */
+static int circumcircle(cplx a, cplx b, cplx c, cplx* centre, double* radius)
+{
+    double ax = creal(a), ay = cimag(a), bx = creal(b), by = cimag(b), cx = creal(c), cy = cimag(c);
+    double d = 2.0 * (ax * (by - cy) + bx * (cy - ay) + cx * (ay - by));
+    if (d == 0.0) return 0;
+    double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    double ux = (a2 * (by - cy) + b2 * (cy - ay) + c2 * (ay - by)) / d;
+    double uy = (a2 * (cx - bx) + b2 * (ax - cx) + c2 * (bx - ax)) / d;
+    *centre = ux + I * uy;
+    *radius = cabs(a - *centre);
+    return 1;
+}
+
+/* Minimum enclosing circle of a point set (the shift that minimises max|v - a|,
+ * i.e. the norm of V0, Sec. 2.3.1 / Sec. 4): Welzl's randomised incremental
+ * algorithm in its iterative form, over a fixed pseudo-random order. */
+static cplx min_enclosing_centre(const cplx* vals, long m)
+{
+    long* idx = malloc(sizeof(long) * m);
+    for (long i = 0; i < m; ++i) idx[i] = i;
+    unsigned long long st = 0x9E3779B97F4A7C15ull;
+    for (long i = m - 1; i > 0; --i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        long j = (long)((st >> 33) % (unsigned long long)(i + 1));
+        long t = idx[i]; idx[i] = idx[j]; idx[j] = t;
+    }
+    const double tol = 1e-12;
+    cplx c = vals[idx[0]];
+    double r = 0.0;
+    for (long i = 1; i < m; ++i) {
+        cplx pi = vals[idx[i]];
+        if (cabs(pi - c) <= r * (1 + tol)) continue;
+        c = pi;
+        r = 0.0;
+        for (long j = 0; j < i; ++j) {
+            cplx pj = vals[idx[j]];
+            if (cabs(pj - c) <= r * (1 + tol)) continue;
+            c = 0.5 * (pi + pj);
+            r = 0.5 * cabs(pi - pj);
+            for (long k = 0; k < j; ++k) {
+                cplx pk = vals[idx[k]];
+                if (cabs(pk - c) <= r * (1 + tol)) continue;
+                cplx cc;
+                double rr;
+                if (circumcircle(pi, pj, pk, &cc, &rr)) { c = cc; r = rr; }
+            }
+        }
+    }
+    free(idx);
+    return c;
+}
+
 /* complex shift over a set of values: 0 = midrange (bounding-box centre),
- * 1 = componentwise median (Algorithm 1's example) */
+ * 1 = componentwise median (Algorithm 1's example), 2 = centre of the minimum
+ * enclosing circle (Sec. 4's recommendation) */
 static cplx choose_shift(const cplx* vals, long m, int rule)
 {
+    if (rule == 2) return min_enclosing_centre(vals, m);
     if (rule == 1) {
         double* re = malloc(sizeof(double) * m);
         double* im = malloc(sizeof(double) * m);

@@ -23,6 +23,7 @@ _lib = None
 
 SHIFT_MIDRANGE = 0
 SHIFT_MEDIAN = 1
+SHIFT_MEC = 2
 
 
 def build(force: bool = False) -> str:

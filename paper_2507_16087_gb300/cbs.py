@@ -15,7 +15,7 @@ from . import build_lib
 
 CBS_OK, CBS_EINVAL, CBS_ENOMEM, CBS_ECUDA, CBS_ENOCONV, CBS_EDIVERGED, CBS_ETIMEOUT = range(7)
 CBS_FP64, CBS_FP32_REFINE, CBS_FP32 = 0, 1, 2
-CBS_SHIFT_MIDRANGE, CBS_SHIFT_MEDIAN = 0, 1
+CBS_SHIFT_MIDRANGE, CBS_SHIFT_MEDIAN, CBS_SHIFT_MEC = 0, 1, 2
 PRECISIONS = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE, "fp32": CBS_FP32}
 STATUS_NAMES = {0: "CBS_OK", 1: "CBS_EINVAL", 2: "CBS_ENOMEM", 3: "CBS_ECUDA", 4: "CBS_ENOCONV",
                 5: "CBS_EDIVERGED", 6: "CBS_ETIMEOUT"}

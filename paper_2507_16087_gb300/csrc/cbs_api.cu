@@ -170,6 +170,51 @@ __global__ void k_setup_values(SetupIn s, double2* dv, double2* qv)
     }
 }
 
+// Support points of a value set: for each of kSupportDirs directions theta_k,
+// the value maximising Re(z e^{-i theta_k}).  Per block: the best value of
+// each direction (projections compared in float32; the values are exact).
+constexpr int kSupportDirs = 64;
+__global__ void k_setup_support(const double2* __restrict__ vals, long long n, double2* __restrict__ best)
+{
+    float bp[kSupportDirs];
+    int bi[kSupportDirs];
+#pragma unroll
+    for (int k = 0; k < kSupportDirs; ++k) { bp[k] = -INFINITY; bi[k] = -1; }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float x = (float)vals[i].x, y = (float)vals[i].y;
+#pragma unroll
+        for (int k = 0; k < kSupportDirs; ++k) {
+            float sk, ck;
+            sincospif(2.0f * (float)k / (float)kSupportDirs, &sk, &ck);
+            const float p = x * ck + y * sk;
+            if (p > bp[k]) { bp[k] = p; bi[k] = (int)i; }
+        }
+    }
+    __shared__ float sp[kSupportDirs][32];
+    __shared__ int si[kSupportDirs][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kSupportDirs; ++k) {
+        float p = bp[k];
+        int ix = bi[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float po = __shfl_down_sync(0xffffffffu, p, o);
+            const int io = __shfl_down_sync(0xffffffffu, ix, o);
+            if (po > p) { p = po; ix = io; }
+        }
+        if (lane == 0) { sp[k][w] = p; si[k][w] = ix; }
+    }
+    __syncthreads();
+    if (threadIdx.x < kSupportDirs) {
+        const int k = threadIdx.x;
+        float p = -INFINITY;
+        int ix = -1;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j)
+            if (si[k][j] >= 0 && sp[k][j] > p) { p = sp[k][j]; ix = si[k][j]; }
+        best[(long long)blockIdx.x * kSupportDirs + k] = ix >= 0 ? vals[ix] : make_double2(NAN, NAN);
+    }
+}
+
 // per-voxel arrays the iteration kernels read: rs_eta = (S+ rho)_eta / lambda1,
 // kp = 1 / (rho c0^2 lambda2), et = 2 alpha c0 / omega  (float64 and float32)
 __global__ void k_setup_store(SetupIn s, double il1, double il2, double* rs64_0, double* rs64_1, double* rs64_2,
@@ -441,6 +486,17 @@ template <typename T> T* dalloc(cbs_solver* s, size_t count)
     }
     s->allocs.push_back(p);
     return static_cast<T*>(p);
+}
+
+// release a set-up temporary before solver_destroy
+void dfree(cbs_solver* s, void* p)
+{
+    auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+    if (it != s->allocs.end()) {
+        cudaStreamSynchronize(s->st);
+        cudaFree(p);
+        s->allocs.erase(it);
+    }
 }
 
 cbs_status set_err(cbs_solver* s, cbs_status code, const std::string& msg)
@@ -846,6 +902,74 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
 }
 
 
+// Minimum enclosing circle (Welzl's randomised incremental algorithm, iterative
+// form, fixed pseudo-random order) of a small host point set: returns the centre.
+double2 mec_centre(std::vector<double2> pts)
+{
+    unsigned long long st = 0x9E3779B97F4A7C15ull;
+    for (size_t i = pts.size(); i > 1; --i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        std::swap(pts[i - 1], pts[(size_t)((st >> 33) % i)]);
+    }
+    auto dist = [](double2 a, double2 b) { return std::hypot(a.x - b.x, a.y - b.y); };
+    auto circ3 = [](double2 a, double2 b, double2 c, double2& ctr, double& r) {
+        const double d = 2.0 * (a.x * (b.y - c.y) + b.x * (c.y - a.y) + c.x * (a.y - b.y));
+        if (d == 0.0) return false;
+        const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y, c2 = c.x * c.x + c.y * c.y;
+        ctr = make_double2((a2 * (b.y - c.y) + b2 * (c.y - a.y) + c2 * (a.y - b.y)) / d,
+                           (a2 * (c.x - b.x) + b2 * (a.x - c.x) + c2 * (b.x - a.x)) / d);
+        r = std::hypot(a.x - ctr.x, a.y - ctr.y);
+        return true;
+    };
+    const double tol = 1e-12;
+    double2 c = pts[0];
+    double r = 0.0;
+    for (size_t i = 1; i < pts.size(); ++i) {
+        if (dist(pts[i], c) <= r * (1 + tol)) continue;
+        c = pts[i];
+        r = 0.0;
+        for (size_t j = 0; j < i; ++j) {
+            if (dist(pts[j], c) <= r * (1 + tol)) continue;
+            c = make_double2(0.5 * (pts[i].x + pts[j].x), 0.5 * (pts[i].y + pts[j].y));
+            r = 0.5 * dist(pts[i], pts[j]);
+            for (size_t k = 0; k < j; ++k) {
+                if (dist(pts[k], c) <= r * (1 + tol)) continue;
+                double2 cc;
+                double rr;
+                if (circ3(pts[i], pts[j], pts[k], cc, rr)) { c = cc; r = rr; }
+            }
+        }
+    }
+    return c;
+}
+
+// centre of the minimum enclosing circle of the support points of a device value set
+double2 support_mec(cbs_solver* s, const double2* vals, long long n)
+{
+    const int g = grid_for(n, kSetupThreads);
+    double2* best = dalloc<double2>(s, (size_t)g * kSupportDirs);
+    k_setup_support<<<g, kSetupThreads, 0, s->st>>>(vals, n, best);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double2> hb((size_t)g * kSupportDirs);
+    CUDA_TRY(cudaMemcpyAsync(hb.data(), best, hb.size() * sizeof(double2), cudaMemcpyDeviceToHost, s->st));
+    CUDA_TRY(cudaStreamSynchronize(s->st));
+    dfree(s, best);
+    std::vector<double2> pts;
+    for (int k = 0; k < kSupportDirs; ++k) {
+        const double ck = std::cos(2.0 * kPi * k / kSupportDirs), sk = std::sin(2.0 * kPi * k / kSupportDirs);
+        double bp = -INFINITY;
+        double2 bv = make_double2(NAN, NAN);
+        for (int b = 0; b < g; ++b) {
+            const double2 v = hb[(size_t)b * kSupportDirs + k];
+            if (std::isnan(v.x)) continue;
+            const double p = v.x * ck + v.y * sk;
+            if (p > bp) { bp = p; bv = v; }
+        }
+        if (!std::isnan(bv.x)) pts.push_back(bv);
+    }
+    return mec_centre(pts);
+}
+
 // Keep the float32 work array resident in L2 across the five kernels of an
 // iteration: an access-policy window marks it persisting (the others stream).
 // The persisting-L2 limit is a property of this process's CUDA context (it
@@ -968,7 +1092,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
     if (!(o.nu > 0 && o.nu < 1) || !(o.beta > 0 && o.beta < 1))
         return set_err(nullptr, CBS_EINVAL, "nu and beta must lie in (0, 1)");
     if (o.precision < CBS_FP64 || o.precision > CBS_FP32) return set_err(nullptr, CBS_EINVAL, "bad precision");
-    if (o.shift_rule != CBS_SHIFT_MIDRANGE && o.shift_rule != CBS_SHIFT_MEDIAN)
+    if (o.shift_rule != CBS_SHIFT_MIDRANGE && o.shift_rule != CBS_SHIFT_MEDIAN && o.shift_rule != CBS_SHIFT_MEC)
         return set_err(nullptr, CBS_EINVAL, "bad shift rule");
     cbs_boundary b{};
     if (boundary) b = *boundary;
@@ -1068,6 +1192,16 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             s->a1i = 0.5 * (mm[2] + mm[3]);
             s->a2r = 0.5 * (mm[4] + mm[5]);
             s->a2i = 0.5 * (mm[6] + mm[7]);
+        } else if (o.shift_rule == CBS_SHIFT_MEC) {
+            double2* dv = dalloc<double2>(s, (size_t)D * N);
+            double2* qv = dalloc<double2>(s, (size_t)N);
+            k_setup_values<<<sg, kSetupThreads, 0, s->st>>>(si, dv, qv);
+            CUDA_TRY(cudaGetLastError());
+            const double2 c1 = support_mec(s, dv, (long long)D * N);
+            const double2 c2 = support_mec(s, qv, (long long)N);
+            s->a1r = c1.x; s->a1i = c1.y; s->a2r = c2.x; s->a2i = c2.y;
+            dfree(s, dv);
+            dfree(s, qv);
         } else {
             double2* dv = dalloc<double2>(s, (size_t)D * N);
             double2* qv = dalloc<double2>(s, (size_t)N);
@@ -1089,6 +1223,8 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             re.clear(); im.clear();
             for (auto& z : hq) { re.push_back(z.x); im.push_back(z.y); }
             s->a2r = median(re); s->a2i = median(im);
+            dfree(s, dv);
+            dfree(s, qv);
         }
         TRACE("create: maxdev");
         k_setup_maxdev<<<sg, kSetupThreads, 0, s->st>>>(si, make_double2(s->a1r, s->a1i), make_double2(s->a2r, s->a2i), part);

@@ -321,3 +321,40 @@ def smooth_random_medium_torch(shape, seed, c_range=(1400.0, 2800.0), rho_range=
     return Problem(name=f"random{len(shape)}d_dev", c0=c0, rho=rho, alpha=alpha, dx=dx, omega=2 * math.pi * f_hz,
                    nabs=[[n_abs, n_abs] for _ in shape], gamma_max=layer_gamma_max(n_abs, dx) if n_abs > 0 else 0.0,
                    meta=dict(seed=seed))
+
+
+def line_source(shape, y_row, amplitude=1.0 + 0j, margin=0):
+    """2D planar line source: s_p = amplitude on every cell of row y_row (x in [margin, n0 - margin))."""
+    src = np.zeros((3,) + tuple(shape), dtype=np.complex128)
+    n0 = shape[1]
+    src[2, y_row, margin:n0 - margin] = amplitude
+    return src
+
+
+def disc_perturbation(n=256, radius=32, dc=0.0, drho=0.0, n_abs=16, ppw=6.0, f_hz=F0):
+    """Convergence-versus-contrast case: water (1500 m/s, 1000 kg/m^3) with a central disc of c = 1500 + dc,
+    rho = 1000 + drho; planar line source near the top (inside the layer's inner edge)."""
+    p = inclusion_medium((n, n), radius, C_WATER + dc, RHO_WATER + drho, 0.0, ppw=ppw, n_abs=n_abs, f_hz=f_hz)
+    p.source = line_source((n, n), n_abs + 2, margin=n_abs)
+    p.name = f"disc_dc{dc:g}_drho{drho:g}"
+    return p
+
+
+def three_discs(n=256, dx=0.5e-3, f_hz=F0, n_abs=16, radius=24):
+    """Strongly heterogeneous 2D example (256 x 256, 0.5 mm, 500 kHz): water with three disc inclusions,
+    one in sound speed (3500 m/s), one in density (3000 kg/m^3), one in attenuation (10 dB/cm), and a planar
+    line source at the top."""
+    shape = (n, n)
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    c0 = np.full(shape, C_WATER)
+    rho = np.full(shape, RHO_WATER)
+    alpha = np.zeros(shape)
+    centres = [(n * 0.3, n * 0.45), (n * 0.7, n * 0.45), (n * 0.5, n * 0.72)]
+    masks = [(xx - cx) ** 2 + (yy - cy) ** 2 < radius ** 2 for cx, cy in centres]
+    c0[masks[0]] = 3500.0
+    rho[masks[1]] = 3000.0
+    alpha[masks[2]] = 10.0 * NEPER_PER_DB * 100.0  # 10 dB/cm in Np/m
+    p = Problem(name="three_discs_256", c0=c0, rho=rho, alpha=alpha, dx=dx, omega=2 * math.pi * f_hz,
+                nabs=[[n_abs, n_abs]] * 2, gamma_max=layer_gamma_max(n_abs, dx))
+    p.source = line_source(shape, n_abs + 2, margin=n_abs)
+    return p

@@ -281,3 +281,28 @@ def test_sphere_128_first_iterations_and_precisions():
     assert s64.residual_norm(f64, T(src)) <= 1.01e-6
     # both are within the stopping tolerance of the same solution
     assert rel(f32.cpu().numpy(), f64.cpu().numpy()) <= 1e-4
+
+
+@pytest.mark.parametrize("rule", ["median", "mec"])
+def test_shift_rules_match_oracle_and_solution(rule):
+    cbs = _cbs()
+    shape = (24, 32)
+    code = {"median": cbs.CBS_SHIFT_MEDIAN, "mec": cbs.CBS_SHIFT_MEC}[rule]
+    orc = {"median": O.SHIFT_MEDIAN, "mec": O.SHIFT_MEC}[rule]
+    p, s, _ = make(shape, seed=34, shift_rule=code, tol=1e-12, check_every=20)
+    P = O.Problem(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, shift_rule=orc)
+    g, o = s.scalars(), P.scalars()
+    if rule == "median":
+        for k in ("a1", "a2", "lambda1", "lambda2"):
+            assert abs(g[k] - o[k]) <= 1e-13 * abs(o[k])
+    else:
+        # support-point circle (64 directions) vs the exact circle: same centre to within the polygon's sag
+        for k, lam in (("a1", "lambda1"), ("a2", "lambda2")):
+            assert abs(g[k] - o[k]) <= 2e-3 * o[lam]
+            assert g[lam] >= o[lam] * (1 - 1e-12)          # exact circle is the smallest
+            assert g[lam] <= o[lam] * (1 + 5e-3)
+    src = W.random_source(shape, 35)
+    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.solve_forward(T(src), field)
+    ref = dense.solve(src, p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power)
+    assert rel(field.cpu().numpy(), ref) <= 1e-10

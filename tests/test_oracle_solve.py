@@ -236,3 +236,49 @@ def test_invalid_inputs_rejected(bad):
         c0[4, 4] = np.nan
     with pytest.raises(ValueError):
         O.Problem(c0, rho, al, 1e-3, 1e6, [[1, 1]] * 2, 1e5)
+
+
+def _mec_brute(pts):
+    """Smallest circle over all pair / triple circles containing every point (O(n^4), tiny n)."""
+    best = (None, np.inf)
+    n = len(pts)
+    cands = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            cands.append(((pts[i] + pts[j]) / 2, abs(pts[i] - pts[j]) / 2))
+            for k in range(j + 1, n):
+                a, b, c = pts[i], pts[j], pts[k]
+                d = 2 * (a.real * (b.imag - c.imag) + b.real * (c.imag - a.imag) + c.real * (a.imag - b.imag))
+                if d == 0:
+                    continue
+                ux = (abs(a) ** 2 * (b.imag - c.imag) + abs(b) ** 2 * (c.imag - a.imag) + abs(c) ** 2 * (a.imag - b.imag)) / d
+                uy = (abs(a) ** 2 * (c.real - b.real) + abs(b) ** 2 * (a.real - c.real) + abs(c) ** 2 * (b.real - a.real)) / d
+                cands.append((ux + 1j * uy, abs(a - (ux + 1j * uy))))
+    for c, r in cands:
+        if r < best[1] and np.all(np.abs(pts - c) <= r * (1 + 1e-9)):
+            best = (c, r)
+    return best
+
+
+def test_mec_shift_is_the_minimum_enclosing_circle():
+    shape = (5, 4)
+    p = _problem(shape, 31, n_abs=1, gamma_scale=0.7)
+    P = _oracle(p, shift_rule=O.SHIFT_MEC)
+    sc = P.scalars()
+    dg, q, _, _ = dense.diagonals(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power)
+    dv = np.concatenate([x.ravel() for x in dg])
+    c1, r1 = _mec_brute(dv)
+    c2, r2 = _mec_brute(q.ravel())
+    assert abs(sc["a1"] - c1) <= 1e-9 * r1 and abs(sc["a2"] - c2) <= 1e-9 * r2
+    # with beta the largest |v| is beta, and no other centre has a smaller enclosing radius
+    assert np.isclose(sc["lambda1"] * 0.95, r1, rtol=1e-9) and np.isclose(sc["lambda2"] * 0.95, r2, rtol=1e-9)
+    Pm = _oracle(p)
+    assert Pm.scalars()["lambda1"] >= sc["lambda1"] * (1 - 1e-12)
+
+
+def test_mec_shift_same_solution():
+    shape = (12, 12)
+    p = _problem(shape, 32)
+    src = W.random_source(shape, 33)
+    f, _, _ = _oracle(p, shift_rule=O.SHIFT_MEC).solve_field(src, 1e-12, check_every=25)
+    assert _rel(f, _dense(p, src)) <= 1e-10
