@@ -55,6 +55,7 @@ typedef enum {
 
 enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1, CBS_FP32 = 2 };
 enum { CBS_SHIFT_MIDRANGE = 0, CBS_SHIFT_MEDIAN = 1, CBS_SHIFT_MEC = 2 };
+enum { CBS_GRID_STAGGERED = 0, CBS_GRID_COLLOCATED = 1 };
 
 typedef struct {
     int ndim;      /* 2 or 3 */
@@ -84,6 +85,9 @@ typedef struct {
     int max_iter;      /* Born iterations (all inner iterations for FP32_REFINE); 0 -> 100000 */
     int check_every;   /* iterations between residual checks; 0 -> 50 */
     void* stream;      /* cudaStream_t the caller's work is queued on (may be 0) */
+    int grid_kind;     /* CBS_GRID_STAGGERED (default, App. B.1: velocity at x + dx/2 e_eta, staggered
+                          density, symbol i k e^{i k dx/2}) or CBS_GRID_COLLOCATED (App. B: velocity at
+                          the cell centres, unshifted density and gamma, symbol i k) */
 } cbs_options;
 
 typedef struct {

@@ -171,6 +171,7 @@ typedef struct orc_problem {
     cplx* inv_rho_c2;   /* [N] 1/(rho c^2), complex c^2 of eq. 118 */
     double* k;          /* [D][nmax] continuous wavenumbers 2 pi fftfreq(n, dx) */
     int64_t kstride;
+    int collocated;     /* 1: velocity at the cell centres (App. B), 0: staggered (App. B.1) */
 } orc_problem;
 
 /* depth of the absorbing layer at continuous cell coordinate xi (reading of
@@ -313,7 +314,7 @@ static cplx choose_shift(const cplx* vals, long m, int rule)
 orc_problem* orc_create(int ndim, const int64_t* n, double dx, double omega,
                         const double* c0, const double* rho, const double* alpha,
                         const int* nabs, double gamma_max, double power,
-                        double beta, int shift_rule)
+                        double beta, int shift_rule, int collocated)
 {
     if (ndim < 1 || ndim > ORC_MAXD || !(dx > 0) || !(omega > 0) || !(beta > 0 && beta < 1)) return NULL;
     orc_problem* P = calloc(1, sizeof(orc_problem));
@@ -323,6 +324,7 @@ orc_problem* orc_create(int ndim, const int64_t* n, double dx, double omega,
     for (int a = 0; a < ndim; ++a) { P->n[a] = n[a]; P->N *= (long)n[a]; }
     P->dx = dx;
     P->omega = omega;
+    P->collocated = collocated;
     const long N = P->N;
     for (long i = 0; i < N; ++i)
         if (!isfinite(c0[i]) || !isfinite(rho[i]) || !isfinite(alpha[i]) || !(c0[i] > 0) || !(rho[i] > 0) || !(alpha[i] >= 0)) {
@@ -353,10 +355,10 @@ orc_problem* orc_create(int ndim, const int64_t* n, double dx, double omega,
         for (int eta = 0; eta < ndim; ++eta) {
             double xs[ORC_MAXD];
             memcpy(xs, xi, sizeof xs);
-            xs[eta] += 0.5;
+            if (!collocated) xs[eta] += 0.5;
             double gs = gamma_at(xs, ndim, n, nabs, gamma_max, power);
-            /* staggered density: mean of the two neighbours along eta */
-            double rs = 0.5 * (rho[i] + rho[neighbour_plus(i, eta, ndim, n)]);
+            /* staggered density: mean of the two neighbours along eta (collocated: rho itself) */
+            double rs = collocated ? rho[i] : 0.5 * (rho[i] + rho[neighbour_plus(i, eta, ndim, n)]);
             P->rho_stag[eta * N + i] = rs;
             /* velocity diagonal: (S+ rho)(S+ gamma + i omega), App. B.1 */
             d[eta * N + i] = rs * (gs + I * omega);
@@ -471,7 +473,8 @@ static void green_matrix(const orc_problem* P, const double* kv, cplx G[ORC_MAXD
     cplx S[ORC_MAXD];
     for (int e = 0; e < D; ++e) {
         k2 += kv[e] * kv[e];
-        S[e] = cexp(I * kv[e] * P->dx / 2.0);
+        /* collocated grid (App. B): no half-cell shift filters */
+        S[e] = P->collocated ? 1.0 : cexp(I * kv[e] * P->dx / 2.0);
     }
     const cplx mu = k2 + (a + l0) * (b + l1);
     const double sq = sqrt(l0 * l1);
@@ -496,7 +499,7 @@ static void l_matrix(const orc_problem* P, const double* kv, cplx Lm[ORC_MAXD + 
     for (int e = 0; e <= D; ++e)
         for (int f = 0; f <= D; ++f) Lm[e][f] = 0;
     for (int e = 0; e < D; ++e) {
-        cplx Se = cexp(I * kv[e] * P->dx / 2.0);
+        cplx Se = P->collocated ? 1.0 : cexp(I * kv[e] * P->dx / 2.0);
         Lm[e][e] = P->a1 / P->lam1;
         Lm[e][D] = I * kv[e] * Se / sq;
         Lm[D][e] = I * kv[e] * conj(Se) / sq;

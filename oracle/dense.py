@@ -58,8 +58,9 @@ def axis_operator(shape, axis_xyz: int, one_d: np.ndarray) -> np.ndarray:
     return M
 
 
-def diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0):
-    """d_eta (D arrays) and q at every voxel, from the formulas in the module docstring."""
+def diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0, collocated=False):
+    """d_eta (D arrays) and q at every voxel, from the formulas in the module docstring (collocated grid of
+    App. B: velocity at the cell centres, so rho and gamma are not shifted)."""
     shape = c0.shape
     D = len(shape)
     c2 = c0 ** 2 / (1 - 2j * alpha * c0 / omega)
@@ -71,33 +72,35 @@ def diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0):
         sh = [1] * D
         sh[D - 1 - a] = n
         per_axis_c.append(layer_profile(n, lo, hi, gamma_max, power, 0.0).reshape(sh))
-        per_axis_s.append(layer_profile(n, lo, hi, gamma_max, power, 0.5).reshape(sh))
+        per_axis_s.append(layer_profile(n, lo, hi, gamma_max, power, 0.0 if collocated else 0.5).reshape(sh))
     gamma = sum(np.broadcast_to(g, shape) for g in per_axis_c)
     q = (1j * omega + gamma) / (rho * c2)
     d = []
     rho_s = []
     for eta in range(D):
         g_s = sum(np.broadcast_to(per_axis_s[a] if a == eta else per_axis_c[a], shape) for a in range(D))
-        r_s = 0.5 * (rho + np.roll(rho, -1, axis=D - 1 - eta))
+        r_s = rho if collocated else 0.5 * (rho + np.roll(rho, -1, axis=D - 1 - eta))
         rho_s.append(r_s)
         d.append(r_s * (g_s + 1j * omega))
     return d, q, rho_s, c2
 
 
-def assemble(c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0, adjoint=False):
-    """Dense row-scaled operator A (C*N x C*N).  adjoint=True gives A^H."""
+def assemble(c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0, adjoint=False, collocated=False):
+    """Dense row-scaled operator A (C*N x C*N).  adjoint=True gives A^H.  collocated: derivative symbol i k
+    (App. B) instead of the staggered i k e^{+-i k dx/2}."""
     shape = c0.shape
     D = len(shape)
     N = int(np.prod(shape))
-    d, q, _, _ = diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power)
+    d, q, _, _ = diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power, collocated)
     A = np.zeros(((D + 1) * N, (D + 1) * N), dtype=np.complex128)
     for eta in range(D):
         n = shape[D - 1 - eta]
         F = dft_matrix(n)
         Fi = np.conj(F).T / n
         k = wavenumbers(n, dx)
-        dplus = Fi @ np.diag(1j * k * np.exp(1j * k * dx / 2)) @ F
-        dminus = Fi @ np.diag(1j * k * np.exp(-1j * k * dx / 2)) @ F
+        sh = 0.0 if collocated else dx / 2
+        dplus = Fi @ np.diag(1j * k * np.exp(1j * k * sh)) @ F
+        dminus = Fi @ np.diag(1j * k * np.exp(-1j * k * sh)) @ F
         A[eta * N:(eta + 1) * N, eta * N:(eta + 1) * N] = np.diag(d[eta].ravel())
         A[eta * N:(eta + 1) * N, D * N:] = axis_operator(shape, eta, dplus)
         A[D * N:, eta * N:(eta + 1) * N] = axis_operator(shape, eta, dminus)
@@ -105,10 +108,10 @@ def assemble(c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0, adjoint=Fals
     return np.conj(A).T if adjoint else A
 
 
-def scaled_rhs(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0):
+def scaled_rhs(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0, collocated=False):
     """Row-scaled right-hand side ((S+ rho) s_u, s_p / (rho c^2))."""
     D = c0.ndim
-    _, _, rho_s, c2 = diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power)
+    _, _, rho_s, c2 = diagonals(c0, rho, alpha, dx, omega, nabs, gamma_max, power, collocated)
     out = np.empty_like(np.asarray(src, dtype=np.complex128))
     for eta in range(D):
         out[eta] = rho_s[eta] * src[eta]
@@ -116,10 +119,10 @@ def scaled_rhs(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0):
     return out
 
 
-def solve(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0):
+def solve(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power=2.0, collocated=False):
     """Physical (u, p) from physical (s_u, s_p) by LAPACK on the dense system."""
-    A = assemble(c0, rho, alpha, dx, omega, nabs, gamma_max, power)
-    b = scaled_rhs(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power).ravel()
+    A = assemble(c0, rho, alpha, dx, omega, nabs, gamma_max, power, collocated=collocated)
+    b = scaled_rhs(src, c0, rho, alpha, dx, omega, nabs, gamma_max, power, collocated).ravel()
     return np.linalg.solve(A, b).reshape(np.shape(src))
 
 

@@ -47,7 +47,7 @@ def _load():
         lib.orc_create.restype = P
         lib.orc_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double, ctypes.c_double,
                                    D, D, D, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double, ctypes.c_int]
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int]
         lib.orc_destroy.argtypes = [P]
         lib.orc_scalars.argtypes = [P, D]
         lib.orc_get_v.argtypes = [P, P]
@@ -109,7 +109,8 @@ class Problem:
     """
 
     def __init__(self, c0, rho, alpha, dx: float, omega: float, nabs, gamma_max: float,
-                 power: float = 2.0, beta: float = 0.95, shift_rule: int = SHIFT_MIDRANGE):
+                 power: float = 2.0, beta: float = 0.95, shift_rule: int = SHIFT_MIDRANGE,
+                 collocated: bool = False):
         lib = _load()
         c0 = np.ascontiguousarray(c0, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -124,7 +125,7 @@ class Problem:
         self._h = lib.orc_create(self.ndim, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(dx), float(omega),
                                  c0.ctypes.data_as(dp), rho.ctypes.data_as(dp), alpha.ctypes.data_as(dp),
                                  nab.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(gamma_max), float(power),
-                                 float(beta), int(shift_rule))
+                                 float(beta), int(shift_rule), int(bool(collocated)))
         if not self._h:
             raise ValueError("oracle set-up rejected the inputs")
         self._lib = lib

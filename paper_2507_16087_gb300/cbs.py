@@ -16,6 +16,7 @@ from . import build_lib
 CBS_OK, CBS_EINVAL, CBS_ENOMEM, CBS_ECUDA, CBS_ENOCONV, CBS_EDIVERGED, CBS_ETIMEOUT = range(7)
 CBS_FP64, CBS_FP32_REFINE, CBS_FP32 = 0, 1, 2
 CBS_SHIFT_MIDRANGE, CBS_SHIFT_MEDIAN, CBS_SHIFT_MEC = 0, 1, 2
+CBS_GRID_STAGGERED, CBS_GRID_COLLOCATED = 0, 1
 PRECISIONS = {"fp64": CBS_FP64, "fp32_refine": CBS_FP32_REFINE, "fp32": CBS_FP32}
 STATUS_NAMES = {0: "CBS_OK", 1: "CBS_EINVAL", 2: "CBS_ENOMEM", 3: "CBS_ECUDA", 4: "CBS_ENOCONV",
                 5: "CBS_EDIVERGED", 6: "CBS_ETIMEOUT"}
@@ -33,7 +34,8 @@ class cbs_boundary(ctypes.Structure):
 class cbs_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("shift_rule", ctypes.c_int), ("tol", ctypes.c_double), ("tol_inner", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("grid_kind", ctypes.c_int)]
 
 
 class cbs_info(ctypes.Structure):
@@ -131,7 +133,7 @@ def _check_field(t, shape):
 def solver_create(c0, rho, alpha, dx: float, omega: float, nabs, gamma_max: float, power: float = 2.0,
                   precision="fp64", nu: float = 0.8, beta: float = 0.95, shift_rule: int = CBS_SHIFT_MIDRANGE,
                   tol: float = 1e-6, tol_inner: float = 1e-4, max_iter: int = 100000, check_every: int = 50,
-                  stream=None):
+                  stream=None, collocated: bool = False):
     """c0, rho, alpha: cuda float64 tensors of the grid shape (n[D-1], ..., n[0])."""
     import torch
     lib = load()
@@ -151,6 +153,7 @@ def solver_create(c0, rho, alpha, dx: float, omega: float, nabs, gamma_max: floa
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.nu, o.beta, o.shift_rule = float(nu), float(beta), int(shift_rule)
     o.tol, o.tol_inner, o.max_iter, o.check_every = float(tol), float(tol_inner), int(max_iter), int(check_every)
+    o.grid_kind = CBS_GRID_COLLOCATED if collocated else CBS_GRID_STAGGERED
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = ctypes.c_void_p(int(stream.cuda_stream))

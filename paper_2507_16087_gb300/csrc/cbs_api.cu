@@ -45,6 +45,7 @@ bool trace_on()
 
 // ---------------------------------------------------------------- set-up kernels
 struct SetupIn {
+    int colloc;  // 1: collocated grid (no half-cell shifts)
     int D, n0, n1, n2;
     long long N;
     double omega;
@@ -65,6 +66,7 @@ __device__ __forceinline__ void unravel(const SetupIn& s, long long i, int& i0, 
 
 __device__ __forceinline__ long long plus_one(const SetupIn& s, int eta, int i0, int i1, int i2)
 {
+    if (s.colloc) return ((long long)i2 * s.n1 + i1) * s.n0 + i0;  // unshifted: the voxel itself
     if (eta == 0) i0 = (i0 + 1) % s.n0;
     else if (eta == 1) i1 = (i1 + 1) % s.n1;
     else i2 = (i2 + 1) % s.n2;
@@ -285,7 +287,7 @@ __global__ void k_medium_gradient(GradIn g, double* __restrict__ grad_c, double*
             // staggered rows at x and at x - e_eta share rho(x) with weight 1/2
             for (int side = 0; side < 2; ++side) {
                 int j0 = i0, j1 = i1, j2 = i2;
-                if (side == 1) {
+                if (side == 1 && !s.colloc) {
                     if (e == 0) j0 = (i0 + s.n0 - 1) % s.n0;
                     else if (e == 1) j1 = (i1 + s.n1 - 1) % s.n1;
                     else j2 = (i2 + s.n2 - 1) % s.n2;
@@ -1092,6 +1094,8 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
     if (!(o.nu > 0 && o.nu < 1) || !(o.beta > 0 && o.beta < 1))
         return set_err(nullptr, CBS_EINVAL, "nu and beta must lie in (0, 1)");
     if (o.precision < CBS_FP64 || o.precision > CBS_FP32) return set_err(nullptr, CBS_EINVAL, "bad precision");
+    if (o.grid_kind != CBS_GRID_STAGGERED && o.grid_kind != CBS_GRID_COLLOCATED)
+        return set_err(nullptr, CBS_EINVAL, "bad grid kind");
     if (o.shift_rule != CBS_SHIFT_MIDRANGE && o.shift_rule != CBS_SHIFT_MEDIAN && o.shift_rule != CBS_SHIFT_MEC)
         return set_err(nullptr, CBS_EINVAL, "bad shift rule");
     cbs_boundary b{};
@@ -1134,13 +1138,15 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             std::vector<float> gc32(n), gs32(n), k232(n);
             std::vector<float2> kt32(n), tw32(n);
             for (int i = 0; i < n; ++i) {
+                const bool colloc = o.grid_kind == CBS_GRID_COLLOCATED;
                 if (a < D) {
                     gc[i] = layer_gamma((double)i, n, b.n_abs[a][0], b.n_abs[a][1], b.gamma_max, b.power);
-                    gs[i] = layer_gamma(i + 0.5, n, b.n_abs[a][0], b.n_abs[a][1], b.gamma_max, b.power);
+                    gs[i] = colloc ? gc[i] : layer_gamma(i + 0.5, n, b.n_abs[a][0], b.n_abs[a][1], b.gamma_max, b.power);
                 }
                 const int f = (i < (n + 1) / 2) ? i : i - n;
                 const double k = 2.0 * kPi * f / (n * dx);
-                kt[i] = make_double2(k * std::cos(k * dx / 2), k * std::sin(k * dx / 2));
+                // t = k e^{i k dx/2} (staggered derivative symbol / i), or k on the collocated grid
+                kt[i] = colloc ? make_double2(k, 0.0) : make_double2(k * std::cos(k * dx / 2), k * std::sin(k * dx / 2));
                 k2[i] = k * k;
                 const double ang = -2.0 * kPi * (double)i / (double)n;
                 tw[i] = make_double2(std::cos(ang), std::sin(ang));
@@ -1163,6 +1169,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             CUDA_TRY(cudaStreamSynchronize(s->st));  // host vectors go out of scope
         }
         SetupIn si;
+        si.colloc = o.grid_kind == CBS_GRID_COLLOCATED ? 1 : 0;
         si.D = D; si.n0 = s->n[0]; si.n1 = s->n[1]; si.n2 = s->n[2]; si.N = N; si.omega = omega;
         si.c0 = c0; si.rho = rho; si.alpha = alpha;
         for (int a = 0; a < 3; ++a) { si.gc[a] = s->gc64[a]; si.gs[a] = s->gs64[a]; }
@@ -1444,6 +1451,7 @@ cbs_status medium_gradient(cbs_solver* s, const double* c0, const double* rho, c
     try {
         begin_call(s);
         GradIn g;
+        g.m.colloc = s->opt.grid_kind == CBS_GRID_COLLOCATED ? 1 : 0;
         g.m.D = s->D; g.m.n0 = s->n[0]; g.m.n1 = s->n[1]; g.m.n2 = s->n[2]; g.m.N = s->N; g.m.omega = s->omega;
         g.m.c0 = c0; g.m.rho = rho; g.m.alpha = alpha;
         for (int a = 0; a < 3; ++a) { g.m.gc[a] = s->gc64[a]; g.m.gs[a] = s->gs64[a]; }

@@ -282,3 +282,20 @@ def test_mec_shift_same_solution():
     src = W.random_source(shape, 33)
     f, _, _ = _oracle(p, shift_rule=O.SHIFT_MEC).solve_field(src, 1e-12, check_every=25)
     assert _rel(f, _dense(p, src)) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (6, 8, 6)])
+def test_collocated_variant_matches_dense_and_symbol_identity(shape):
+    """App. B's collocated grid: the Born fixed point equals the dense collocated system; (L+I)^-1 inverts L+I."""
+    p = _problem(shape, 37)
+    src = W.random_source(shape, 38)
+    P = _oracle(p, collocated=True)
+    f, _, _ = P.solve_field(src, 1e-12, check_every=25)
+    ref = dense.solve(src, p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power, collocated=True)
+    assert _rel(f, ref) <= 1e-10
+    # differs from the staggered solution (the variant changes the discretisation)
+    assert _rel(f, _dense(p, src)) > 1e-4
+    x = W.random_source(shape, 39)
+    v = P.v()
+    Lx = P.apply(x) - v * x
+    assert np.max(np.abs(P.green(Lx + x) - x)) <= 1e-12 * np.max(np.abs(x))
