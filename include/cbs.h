@@ -50,7 +50,7 @@ typedef enum {
     CBS_ECUDA = 3,      /* a CUDA call failed */
     CBS_ENOCONV = 4,    /* max_iter reached before tol; field holds the last iterate */
     CBS_EDIVERGED = 5,  /* non-finite or growing iterate; field holds the last finite iterate */
-    CBS_ETIMEOUT = 6    /* reserved */
+    CBS_ETIMEOUT = 6    /* a staged bulk copy did not complete within its bounded wait */
 } cbs_status;
 
 enum { CBS_FP64 = 0, CBS_FP32_REFINE = 1, CBS_FP32 = 2 };
@@ -205,6 +205,17 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
  * overlap on the GPU race and must be serialised by the caller. */
 cbs_status green_apply_noalloc(const cbs_grid* grid, double dx, const double* scalars, const void* in, void* out,
                                int adjoint, void* stream);
+
+/* Failure-detection self-test (no counterpart in the paper).  which =
+ * CBS_SELFTEST_BULK_TIMEOUT launches one block whose bulk copy delivers half
+ * the bytes its shared-memory barrier expects, so the barrier never completes:
+ * the kernel's bounded wait gives up, records the timeout in an error word and
+ * returns, as the Born row kernels do.  *result = CBS_ETIMEOUT when the wait
+ * expired and was reported, CBS_OK otherwise.  Returns CBS_ECUDA if a CUDA
+ * call failed (the context stays usable after a timeout).  Allocates and
+ * frees 24 bytes of device memory. */
+enum { CBS_SELFTEST_BULK_TIMEOUT = 1 };
+cbs_status cbs_selftest(int which, int* result);
 
 void solver_destroy(cbs_solver* s);
 

@@ -55,7 +55,7 @@ class cbs_info(ctypes.Structure):
 
 EXPORTS = ("solver_create", "solve_forward", "solve_adjoint", "residual_norm", "born_iterate", "green_apply",
            "operator_apply", "scale_source", "unscale_field", "solver_scalars", "solver_time_kernels",
-           "solver_destroy", "cbs_last_error", "green_apply_noalloc", "medium_gradient")
+           "solver_destroy", "cbs_last_error", "green_apply_noalloc", "medium_gradient", "cbs_selftest")
 
 _lock = threading.Lock()
 _lib = None
@@ -109,9 +109,25 @@ def load(path: str | None = None):
         lib.medium_gradient.argtypes = [V, V, V, V, V, V, V, V, V, I]
         lib.green_apply_noalloc.restype = S
         lib.green_apply_noalloc.argtypes = [ctypes.POINTER(cbs_grid), D, ctypes.POINTER(D), V, V, I, V]
+        lib.cbs_selftest.restype = S
+        lib.cbs_selftest.argtypes = [I, ctypes.POINTER(I)]
         if path is None:
             _lib = lib
         return lib
+
+
+CBS_SELFTEST_BULK_TIMEOUT = 1
+
+
+def selftest_bulk_timeout() -> int:
+    """Run the bulk-copy timeout self-test on the current device: a barrier that never completes makes the
+    kernel's bounded wait expire.  Returns CBS_ETIMEOUT when the kernel noticed and reported it."""
+    lib = load()
+    out = ctypes.c_int(-1)
+    st = lib.cbs_selftest(CBS_SELFTEST_BULK_TIMEOUT, ctypes.byref(out))
+    if st != CBS_OK:
+        raise CBSError(st, "self-test launch failed")
+    return out.value
 
 
 class CBSError(RuntimeError):

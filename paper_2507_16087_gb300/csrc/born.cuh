@@ -21,6 +21,8 @@
 //   v_p   = kp [(gamma + et omega) + i (omega - gamma et)] - a2/lambda2
 // (eq. LV with q = (i omega + gamma)/(rho c^2), c^2 of eq. 118).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the tensor-copy descriptor type; no driver calls here)
+
 #include "fft.cuh"
 
 namespace cbs {
@@ -484,11 +486,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
 
 constexpr int kBulkWaitLimit = 1 << 22;  // try_wait rounds before a copy is declared lost
 constexpr int kErrBulkTimeout = 1;
+constexpr int kErrTileAlign = 2;  // a shared-memory tile not on the 128-byte boundary tensor copies want
 
 // true when the phase completed; false after kBulkWaitLimit rounds
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int limit = kBulkWaitLimit)
 {
-    for (int i = 0; i < kBulkWaitLimit; ++i)
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
 }
@@ -646,6 +649,150 @@ k_rows_inv_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, cplx<R>* __restric
         s1 += cabs2(xn);
     }
     block_sum2(s0, s1, partials + 2 * (long long)blockIdx.x);
+}
+
+// ------------------------------------------ tensor-copy helpers (3D tiles)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// returns once the committed stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// orders this thread's shared-memory writes before later tensor copies that read them
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------ last_symbol, tile-staged
+// The k_last_symbol step for 3D fields, with the block's data staged in shared
+// memory: the tile [C][NL][COLS] (COLS x-columns at one y, all z, all C
+// components) arrives by one tensor copy per component, each on its own
+// mbarrier.  The C forward transforms along z run one after the other out of
+// the tile (each result written back in natural order), the per-wavenumber
+// symbol updates the tile in place, the inverse transforms run the same way,
+// and the tile leaves by tensor stores.  Only one component's RL values are in
+// registers at a time.  tmap describes the field as {n0, n1, C*n2} 8-byte
+// elements with box {COLS, 1, NL}; n0 % COLS == 0.
+// grid: n1 * (n0 / COLS); block: (NL / RL) * COLS.
+template <typename R, int NL, int RL, int COLS, int C> struct LastTileCfg {
+    static constexpr int T = NL / RL;
+    static constexpr int THREADS = T * COLS;
+    static constexpr int TILE = NL * COLS;
+    static constexpr uint32_t TILE_BYTES = TILE * sizeof(cplx<R>);
+    static constexpr size_t SMEM = (size_t)C * TILE_BYTES + C * sizeof(uint64_t);
+};
+
+template <typename R, int NL, int RL, int COLS, int C>
+__global__ void __launch_bounds__(LastTileCfg<R, NL, RL, COLS, C>::THREADS)
+k_last_symbol_tile(const __grid_constant__ CUtensorMap tmap, Dims d, Symbol<R> Sy, const cplx<R>* __restrict__ tw,
+                   int mode, int* err)
+{
+    using CT = cplx<R>;
+    using Cfg = LastTileCfg<R, NL, RL, COLS, C>;
+    constexpr int T = Cfg::T;
+    constexpr int D = C - 1;
+    constexpr int TILE = Cfg::TILE;
+    constexpr int np = plan_npass(NL, RL);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    CT* tile = reinterpret_cast<CT*>(smraw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + (size_t)C * Cfg::TILE_BYTES);
+    const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    const int xblocks = d.n0 / COLS;
+    const int x0 = (blockIdx.x % xblocks) * COLS;
+    const int i1 = blockIdx.x / xblocks;
+    if (smem_u32(smraw) & 127u) {  // block-uniform; no copy has been issued
+        if (threadIdx.x == 0) atomicExch(err, kErrTileAlign);
+        return;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) mbar_init(&bar[c], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            mbar_expect_tx(&bar[c], Cfg::TILE_BYTES);
+            tma_load_3d(tile + c * TILE, &tmap, x0, i1, c * NL, &bar[c]);
+        }
+    }
+    TwCache<NL, RL, CT> tc;
+    tw_load<NL, RL, T>(tc, t, tw);
+    // forward transforms along z, one component at a time
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const bool ok = mbar_wait_bounded(&bar[c], 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, kErrBulkTimeout);
+                for (int k = c; k < C; ++k) mbar_wait_bounded(&bar[k], 0);
+            }
+            return;
+        }
+        CT* tcp = tile + c * TILE;
+        CT v[RL];
+#pragma unroll
+        for (int s = 0; s < RL; ++s) v[s] = tcp[(t + T * slot_q<NL, RL, 0>(s)) * COLS + col];
+        fft_run<NL, RL, -1>(v, tcp + col, COLS, t, tw, tc, BlockSync());
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < RL; ++s) tcp[(t + T * slot_q<NL, RL, np>(s)) * COLS + col] = v[s];
+    }
+    __syncthreads();
+    // per-wavenumber symbol on all C components (each position read and written by one thread)
+    {
+        const int ix = x0 + col;
+        CT tx[D];
+        R k2c = Sy.k2[0][ix];
+        tx[0] = Sy.kt[0][ix];
+        if (D == 3) {
+            tx[1] = Sy.kt[1][i1];
+            k2c += Sy.k2[1][i1];
+        }
+#pragma unroll 2
+        for (int s = 0; s < RL; ++s) {
+            const int iz = t + T * s;
+            tx[D - 1] = Sy.kt[D - 1][iz];
+            const R k2 = k2c + Sy.k2[D - 1][iz];
+            CT vv[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) vv[c] = tile[c * TILE + iz * COLS + col];
+            apply_symbol<R, C>(Sy, mode, tx, k2, vv);
+#pragma unroll
+            for (int c = 0; c < C; ++c) tile[c * TILE + iz * COLS + col] = vv[c];
+        }
+    }
+    // inverse transforms, one component at a time
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if (c == 0) __syncthreads();
+        CT* tcp = tile + c * TILE;
+        CT v[RL];
+#pragma unroll
+        for (int s = 0; s < RL; ++s) v[s] = tcp[(t + T * slot_q<NL, RL, 0>(s)) * COLS + col];
+        fft_run<NL, RL, +1>(v, tcp + col, COLS, t, tw, tc, BlockSync());
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < RL; ++s) tcp[(t + T * slot_q<NL, RL, np>(s)) * COLS + col] = v[s];
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) tma_store_3d(&tmap, tile + c * TILE, x0, i1, c * NL);
+        bulk_commit();
+        bulk_wait_read_all();
+    }
 }
 
 }  // namespace cbs

@@ -3,6 +3,8 @@
 // operator entry points used for step-by-step checks.  All compute runs in
 // the kernels of born.cuh and the set-up/utility kernels below; the host
 // only computes O(n) per-axis tables and scalars.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -880,7 +882,7 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
         if (herr != 0) {
             CUDA_TRY(cudaMemsetAsync(s->errword, 0, sizeof(int), s->st));
             CUDA_TRY(cudaStreamSynchronize(s->st));
-            st = CBS_ETIMEOUT;
+            st = herr == kErrTileAlign ? CBS_ECUDA : CBS_ETIMEOUT;
         }
         float ms = 0;
         CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
@@ -895,6 +897,7 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
         if (st == CBS_ENOCONV) s->err = "max_iter reached before tol";
         if (st == CBS_EDIVERGED) s->err = "iteration produced a non-finite value";
         if (st == CBS_ETIMEOUT) s->err = "a bulk copy did not complete within its wait limit";
+        if (herr == kErrTileAlign) s->err = "shared-memory tile not 128-byte aligned for tensor copies";
         return st;
     } catch (const CudaError& e) {
         return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
@@ -1001,6 +1004,47 @@ void set_l2_window(cbs_solver* s, void* base, size_t bytes)
     cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor-copy descriptor of the float32 work field for the tile-staged last-axis kernel: the field
+// [C][n2][n1][n0] seen as {n0, n1, C*n2} 8-byte elements, box {COLS, 1, n2}.  Leaves tile_field null
+// (register kernel) when the sizes do not qualify, the descriptor cannot be made, or the environment
+// variable CBS_NO_TILE_LAST is set.
+template <typename R> void fill_tile_map(cbs_solver* s, Plan<R>& P, const void* field)
+{
+    P.tile_field = nullptr;
+    const int n2 = s->n[2];
+    if (s->D != 3 || field == nullptr || !tile_ok<R>(n2) || s->n[0] % cols_tile<R>(n2) != 0) return;
+    if (std::getenv("CBS_NO_TILE_LAST") != nullptr) return;
+    auto enc = tensor_map_encoder();
+    if (!enc) return;
+    const cuuint64_t gdim[3] = {(cuuint64_t)s->n[0], (cuuint64_t)s->n[1], (cuuint64_t)s->C * n2};
+    const cuuint64_t gstride[2] = {(cuuint64_t)s->n[0] * sizeof(cplx<R>),
+                                   (cuuint64_t)s->n[0] * s->n[1] * sizeof(cplx<R>)};
+    const cuuint32_t box[3] = {(cuuint32_t)cols_tile<R>(n2), 1u, (cuuint32_t)n2};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    static_assert(sizeof(cplx<R>) == 8, "the descriptor treats one complex value as one 8-byte element");
+    const CUresult r = enc(&P.tmap_last, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(field), gdim, gstride,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS) P.tile_field = field;
+    TRACE("tile map for the last axis: %s", r == CUDA_SUCCESS ? "yes" : "no");
+}
+
 template <typename R> void fill_plan(cbs_solver* s, Plan<R>& P)
 {
     P.d.D = s->D;
@@ -1041,6 +1085,28 @@ template <typename R> void fill_plan(cbs_solver* s, Plan<R>& P)
     P.Sy.la2 = mk<cplx<R>, R>((R)(s->a2r / l2), (R)(s->a2i / l2));
     P.Sy.isq = (R)(1.0 / sq);
     P.Sy.scale = (R)scale;
+}
+
+// Failure-detection self-test: thread 0 arms the barrier for two elements but
+// the bulk copy sends one, so the phase never completes.  The bounded wait
+// gives up after `limit` rounds, the kernel records the timeout in the error
+// word and returns; nothing faults and the context stays usable.  The one copy
+// that was issued has landed by then (16 bytes from device memory).
+__global__ void k_selftest_bulk_timeout(const double2* src, int* err, int* out, int limit)
+{
+    __shared__ __align__(128) double2 buf[2];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, 2 * sizeof(double2));
+        bulk_g2s(buf, src, sizeof(double2), &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, limit);
+    if (threadIdx.x == 0) {
+        if (!ok) atomicExch(err, kErrBulkTimeout);
+        out[0] = ok ? 0 : 1;
+    }
 }
 
 }  // namespace
@@ -1271,6 +1337,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         TRACE("create: plans");
         fill_plan<double>(s, s->P64);
         fill_plan<float>(s, s->P32);
+        fill_tile_map<float>(s, s->P32, s->w32);
         const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)), grid_for(n));
         s->npart = nb;
         s->kslots = std::min(o.check_every, kHostBuf / 2);
@@ -1539,6 +1606,29 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
     } catch (const CudaError& e) {
         return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
     }
+}
+
+cbs_status cbs_selftest(int which, int* result)
+{
+    if (!result || which != CBS_SELFTEST_BULK_TIMEOUT) return CBS_EINVAL;
+    double2* src = nullptr;
+    int* words = nullptr;
+    cudaError_t e = cudaMalloc(&src, sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&words, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(src, 0, sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemset(words, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+        k_selftest_bulk_timeout<<<1, 32>>>(src, words, words + 1, 256);
+        e = cudaGetLastError();
+    }
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, words, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(src);
+    cudaFree(words);
+    if (e != cudaSuccess) return CBS_ECUDA;
+    *result = (h[0] == kErrBulkTimeout && h[1] == 1) ? CBS_ETIMEOUT : CBS_OK;
+    return CBS_OK;
 }
 
 }  // extern "C"

@@ -31,6 +31,14 @@ template <typename R> __host__ __device__ constexpr int cols_last(int n)
                           : (n <= 128 ? 8 : (n <= 256 ? 4 : (n <= 512 ? 2 : (n <= 1024 ? 2 : 1))));
 }
 
+// tile-staged last-axis kernel (3D float32, 16 <= n2 <= 256: one tensor-copy box per component)
+template <typename R> __host__ __device__ constexpr int r_tile(int n) { return (n % 3 == 0) ? 6 : 8; }
+template <typename R> __host__ __device__ constexpr int cols_tile(int n) { return n <= 64 ? 32 : (n <= 128 ? 16 : 8); }
+template <typename R> __host__ __device__ constexpr bool tile_ok(int n)
+{
+    return sizeof(R) == 4 && n >= 16 && n <= 256;
+}
+
 #define CBS_FOR_EACH_SIZE(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024) X(2048)
 
 inline bool size_supported(long long n)
@@ -51,6 +59,10 @@ template <typename R> struct Plan {
     Symbol<R> Sy;
     const cplx<R>* tw[3];  // twiddle table of each axis length
     int* err = nullptr;    // device error word of the bulk-staged kernels (nullptr: plain kernels only)
+    // tensor-copy descriptor of one work field for the tile-staged last-axis kernel; used when the kernel
+    // is given that field (tile_field) and the error word is set
+    CUtensorMap tmap_last;
+    const void* tile_field = nullptr;
 };
 
 // the Born row kernels stage their rows with bulk copies when every block's
@@ -139,8 +151,27 @@ template <typename R, int N, int S> cudaError_t axis_n(const Plan<R>& P, cplx<R>
     return cudaGetLastError();
 }
 
+template <typename R, int N, int C> cudaError_t last_tile_n(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st)
+{
+    constexpr int RL = r_tile<R>(N);
+    constexpr int COLS = cols_tile<R>(N);
+    using Cfg = LastTileCfg<R, N, RL, COLS, C>;
+    auto kern = k_last_symbol_tile<R, N, RL, COLS, C>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    const long long grid = (long long)P.d.n1 * (P.d.n0 / COLS);
+    kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, st>>>(P.tmap_last, P.d, P.Sy, P.tw[2], mode, P.err);
+    return cudaGetLastError();
+}
+
 template <typename R, int N, int C> cudaError_t last_n(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st)
 {
+    if constexpr (C == 4 && tile_ok<R>(N)) {
+        if (P.tile_field != nullptr && P.tile_field == (const void*)w && P.err != nullptr &&
+            P.d.n0 % cols_tile<R>(N) == 0)
+            return last_tile_n<R, N, C>(P, w, mode, st);
+    }
     constexpr int RL = r_last<R>(N);
     constexpr int COLS = cols_last<R>(N);
     constexpr int T = N / RL;

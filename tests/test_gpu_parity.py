@@ -329,3 +329,38 @@ def test_collocated_grid_matches_oracle(shape):
     s.solve_forward(T(v), field)
     ref = dense.solve(v, p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power, collocated=True)
     assert rel(field.cpu().numpy(), ref) <= 1e-10
+
+
+def test_bulk_copy_wait_expires_and_reports():
+    """Failure detection without a fault: a bulk copy that delivers half the bytes its barrier expects never
+    completes the phase; the bounded wait gives up, the kernel reports CBS_ETIMEOUT and returns, and the
+    context still computes correctly afterwards."""
+    cbs = _cbs()
+    assert cbs.selftest_bulk_timeout() == cbs.CBS_ETIMEOUT
+    _, s, P = make((16, 16), seed=2)
+    v = W.random_source((16, 16), 3)
+    out = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.green_apply(T(v), out)
+    assert rel(out.cpu().numpy(), P.green(v)) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (128, 32, 48), (96, 24, 32), (192, 8, 16), (256, 16, 16),
+                                   (16, 24, 32)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_last_axis_tile_kernel_matches_register_kernel_and_oracle(shape, adjoint, monkeypatch):
+    """The tile-staged last-axis kernel (tensor copies into shared memory, one component transformed at a
+    time) does the same arithmetic in the same order as the all-in-registers kernel: float32 Born
+    iterations agree to float32 rounding (contraction into FMAs may differ), and both match the float64
+    oracle."""
+    _, s, P = make(shape, seed=40, precision="fp32")
+    monkeypatch.setenv("CBS_NO_TILE_LAST", "1")
+    _, s_reg, _ = make(shape, seed=40, precision="fp32")
+    monkeypatch.delenv("CBS_NO_TILE_LAST")
+    y = P.scale_source(W.random_source(shape, 41), adjoint)
+    x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    x_reg = torch.zeros_like(x)
+    s.born_iterate(T(y), x, 12, adjoint)
+    s_reg.born_iterate(T(y), x_reg, 12, adjoint)
+    assert rel(x.cpu().numpy(), x_reg.cpu().numpy()) <= 1e-6
+    xr, _ = P.iterate(y, n_iter=12, nu=0.5, adjoint=adjoint)
+    assert rel(x.cpu().numpy(), xr) <= 1e-5
