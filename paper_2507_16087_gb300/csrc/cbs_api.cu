@@ -559,13 +559,23 @@ void reduce_slots(cbs_solver* s, int nblk, int nslots, double* out)
 
 // one Born iteration on the precision-R buffers (eq. BornAlt); its norm
 // partials go to slot `slot`
+template <typename R> int iter_blocks(const Plan<R>& P) { return P.plane ? plane_blocks<R>(P) : rows_blocks<R>(P); }
+template <typename R> int iter_kernels(const Plan<R>& P) { return P.plane ? 3 : (P.d.D == 3 ? 5 : 3); }
+
 template <typename R> void iterate_once(cbs_solver* s, bool adj, int slot)
 {
     Plan<R>& P = Bufs<R>::plan(s);
     auto x = Bufs<R>::x(s);
     auto y = Bufs<R>::y(s);
     auto w = Bufs<R>::w(s);
-    const int nblk = rows_blocks<R>(P);
+    const int nblk = iter_blocks<R>(P);
+    if (P.plane) {  // x-y plane kernels around the last-axis symbol kernel
+        CUDA_TRY(launch_plane_fwd<R>(P, x, y, w, adj, s->st));
+        CUDA_TRY(launch_last<R>(P, w, adj ? SYM_GREEN_ADJ : SYM_GREEN, s->st));
+        CUDA_TRY(launch_plane_inv<R>(P, x, w, adj, (R)s->opt.nu, s->partials + (size_t)slot * nblk * 2, s->st));
+        s->launches += 3;
+        return;
+    }
     CUDA_TRY(launch_rows_fwd<R>(P, x, y, w, FWD_BORN, adj, s->st));
     if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, -1, s->st));
     CUDA_TRY(launch_last<R>(P, w, adj ? SYM_GREEN_ADJ : SYM_GREEN, s->st));
@@ -578,7 +588,7 @@ template <typename R> void iterate_once(cbs_solver* s, bool adj, int slot)
 template <typename R> void iterate_block(cbs_solver* s, int n, bool adj)
 {
     for (int k = 0; k < n; ++k) iterate_once<R>(s, adj, k);
-    reduce_slots(s, rows_blocks<R>(Bufs<R>::plan(s)), n, s->hist);
+    reduce_slots(s, iter_blocks<R>(Bufs<R>::plan(s)), n, s->hist);
 }
 
 // run n iterations in blocks of K = kslots; full blocks replay a captured CUDA graph
@@ -625,7 +635,7 @@ template <typename R> void run_iterations(cbs_solver* s, int n, bool adj)
                 CUDA_TRY(e);
             }
             CUDA_TRY(cudaGraphLaunch(ge, s->st));
-            s->launches += (long long)K * ((s->D == 3) ? 5 : 3) + 1;
+            s->launches += (long long)K * iter_kernels<R>(Bufs<R>::plan(s)) + 1;
         }
         s->hist_n = blk;
         n -= blk;
@@ -1338,7 +1348,9 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         fill_plan<double>(s, s->P64);
         fill_plan<float>(s, s->P32);
         fill_tile_map<float>(s, s->P32, s->w32);
-        const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)), grid_for(n));
+        s->P32.plane = o.precision != CBS_FP64 && plane_ok<float>(s->P32) && std::getenv("CBS_PLANE") != nullptr;
+        const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)),
+                                std::max(grid_for(n), plane_blocks<float>(s->P32)));
         s->npart = nb;
         s->kslots = std::min(o.check_every, kHostBuf / 2);
         TRACE("create: partials %d x %d", nb, s->kslots);
@@ -1549,8 +1561,10 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
     const bool f32 = s->opt.precision != CBS_FP64;
     const char* kn3[5] = {"rows_fwd", "axis_fwd", "last_symbol", "axis_inv", "rows_inv"};
     const char* kn2[3] = {"rows_fwd", "last_symbol", "rows_inv"};
-    const int K = s->D == 3 ? 5 : 3;
-    const char** kn = s->D == 3 ? kn3 : kn2;
+    const char* knp[3] = {"plane_fwd", "last_symbol", "plane_inv"};
+    const bool plane = f32 && s->P32.plane;
+    const int K = (s->D == 3 && !plane) ? 5 : 3;
+    const char** kn = plane ? knp : (s->D == 3 ? kn3 : kn2);
     try {
         begin_call(s);
         const long long n = field_len(s);
@@ -1570,6 +1584,18 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
             mark();
             if (f32) {
                 Plan<float>& P = s->P32;
+                if (plane) {
+                    CUDA_TRY(launch_plane_fwd<float>(P, s->x32, s->y32, s->w32, 0, s->st)); mark();
+                    CUDA_TRY(launch_last<float>(P, s->w32, SYM_GREEN, s->st)); mark();
+                    CUDA_TRY(launch_plane_inv<float>(P, s->x32, s->w32, 0, (float)s->opt.nu, s->partials, s->st)); mark();
+                    CUDA_TRY(cudaStreamSynchronize(s->st));
+                    for (int j = 0; j < K; ++j) {
+                        float tj = 0;
+                        CUDA_TRY(cudaEventElapsedTime(&tj, ev[j], ev[j + 1]));
+                        acc[j] += tj;
+                    }
+                    continue;
+                }
                 CUDA_TRY(launch_rows_fwd<float>(P, s->x32, s->y32, s->w32, FWD_BORN, 0, s->st)); mark();
                 if (s->D == 3) { CUDA_TRY(launch_axis<float>(P, s->w32, -1, s->st)); mark(); }
                 CUDA_TRY(launch_last<float>(P, s->w32, SYM_GREEN, s->st)); mark();

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "born.cuh"
+#include "plane.cuh"
 
 namespace cbs {
 
@@ -63,7 +64,17 @@ template <typename R> struct Plan {
     // is given that field (tile_field) and the error word is set
     CUtensorMap tmap_last;
     const void* tile_field = nullptr;
+    bool plane = false;    // the Born iteration uses the x-y plane kernels (see plane_ok)
 };
+
+// x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane
+constexpr int kPlaneCL = 2;
+inline bool plane_size(int n) { return n == 32 || n == 64 || n == 128; }
+template <typename R> inline bool plane_ok(const Plan<R>& P)
+{
+    return sizeof(R) == 4 && P.d.D == 3 && plane_size(P.d.n0) && plane_size(P.d.n1);
+}
+template <typename R> inline int plane_blocks(const Plan<R>& P) { return (P.d.D + 1) * P.d.n2 * kPlaneCL; }
 
 // the Born row kernels stage their rows with bulk copies when every block's
 // rows lie in one component and the rows' exchange fits in place
@@ -236,6 +247,73 @@ template <typename R> cudaError_t launch_last(const Plan<R>& P, cplx<R>* w, int 
     }
 }
 
+template <typename Kern, typename... Args>
+cudaError_t launch_clustered(Kern kern, int grid, int threads, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kPlaneCL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = kPlaneCL > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename R, int NX, int NY>
+cudaError_t plane_fwd_n(const Plan<R>& P, const cplx<R>* x, const cplx<R>* y, cplx<R>* w, int adj, cudaStream_t st)
+{
+    using Cfg = PlaneCfg<R, NX, NY, kPlaneCL>;
+    auto kern = k_plane_fwd<R, NX, NY, kPlaneCL>;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    return launch_clustered(kern, plane_blocks<R>(P), Cfg::THREADS, Cfg::SMEM, st, P.d, P.M, x, y, w, P.tw[0],
+                            P.tw[1], adj);
+}
+
+template <typename R, int NX, int NY>
+cudaError_t plane_inv_n(const Plan<R>& P, cplx<R>* x, const cplx<R>* w, int adj, R nu, double* partials, cudaStream_t st)
+{
+    using Cfg = PlaneCfg<R, NX, NY, kPlaneCL>;
+    auto kern = k_plane_inv<R, NX, NY, kPlaneCL>;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    return launch_clustered(kern, plane_blocks<R>(P), Cfg::THREADS, Cfg::SMEM, st, P.d, P.M, x, w, P.tw[0], P.tw[1],
+                            adj, nu, partials);
+}
+
+#define CBS_FOR_EACH_PLANE(X) X(32, 32) X(32, 64) X(32, 128) X(64, 32) X(64, 64) X(64, 128) X(128, 32) X(128, 64) X(128, 128)
+
+// w = FFT_y FFT_x (B x + y) over every (component, z) plane
+template <typename R>
+cudaError_t launch_plane_fwd(const Plan<R>& P, const cplx<R>* x, const cplx<R>* y, cplx<R>* w, int adj, cudaStream_t st)
+{
+    if constexpr (sizeof(R) == 4) {
+#define CBS_CASE(a, b) if (P.d.n0 == a && P.d.n1 == b) return plane_fwd_n<R, a, b>(P, x, y, w, adj, st);
+        CBS_FOR_EACH_PLANE(CBS_CASE)
+#undef CBS_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+// x += nu B (IFFT_x IFFT_y w - x) over every plane; norm partials per block
+template <typename R>
+cudaError_t launch_plane_inv(const Plan<R>& P, cplx<R>* x, const cplx<R>* w, int adj, R nu, double* partials,
+                             cudaStream_t st)
+{
+    if constexpr (sizeof(R) == 4) {
+#define CBS_CASE(a, b) if (P.d.n0 == a && P.d.n1 == b) return plane_inv_n<R, a, b>(P, x, w, adj, nu, partials, st);
+        CBS_FOR_EACH_PLANE(CBS_CASE)
+#undef CBS_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
 // explicit instantiation helper
 #define CBS_INSTANTIATE_LAUNCHERS(R)                                                                                 \
     template int rows_blocks<R>(const Plan<R>&);                                                                     \
@@ -244,7 +322,10 @@ template <typename R> cudaError_t launch_last(const Plan<R>& P, cplx<R>* w, int 
     template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R, double*, \
                                             cudaStream_t);                                                           \
     template cudaError_t launch_axis<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                                \
-    template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);
+    template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                                \
+    template cudaError_t launch_plane_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int,          \
+                                             cudaStream_t);                                                          \
+    template cudaError_t launch_plane_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, int, R, double*, cudaStream_t);
 
 }  // namespace cbs
 
@@ -257,5 +338,9 @@ namespace cbs {
     extern template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R,   \
                                                    double*, cudaStream_t);                                           \
     extern template cudaError_t launch_axis<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                         \
-    extern template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);
+    extern template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                         \
+    extern template cudaError_t launch_plane_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int,   \
+                                                    cudaStream_t);                                                   \
+    extern template cudaError_t launch_plane_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, int, R, double*,       \
+                                                    cudaStream_t);
 }  // namespace cbs
