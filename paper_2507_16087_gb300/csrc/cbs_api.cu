@@ -1031,15 +1031,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 // Tensor-copy descriptor of the float32 work field for the tile-staged last-axis kernel: the field
-// [C][n2][n1][n0] seen as {n0, n1, C*n2} 8-byte elements, box {COLS, 1, n2}.  Leaves tile_field null
-// (register kernel) when the sizes do not qualify, the descriptor cannot be made, or the environment
-// variable CBS_NO_TILE_LAST is set.
+// [C][n2][n1][n0] seen as {n0, n1, C*n2} 8-byte elements, box {COLS, 1, n2}.  The tile kernel is
+// opt-in (environment variable CBS_TILE_LAST): on GB300 it measured no faster than the register
+// kernel (41.0 us at 128^3) and slower at 64^3 and 256^3.  Leaves tile_field null (register kernel)
+// when not asked for, when the sizes do not qualify, or when the descriptor cannot be made.
 template <typename R> void fill_tile_map(cbs_solver* s, Plan<R>& P, const void* field)
 {
     P.tile_field = nullptr;
     const int n2 = s->n[2];
     if (s->D != 3 || field == nullptr || !tile_ok<R>(n2) || s->n[0] % cols_tile<R>(n2) != 0) return;
-    if (std::getenv("CBS_NO_TILE_LAST") != nullptr) return;
+    if (std::getenv("CBS_TILE_LAST") == nullptr) return;
     auto enc = tensor_map_encoder();
     if (!enc) return;
     const cuuint64_t gdim[3] = {(cuuint64_t)s->n[0], (cuuint64_t)s->n[1], (cuuint64_t)s->C * n2};
@@ -1348,7 +1349,9 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         fill_plan<double>(s, s->P64);
         fill_plan<float>(s, s->P32);
         fill_tile_map<float>(s, s->P32, s->w32);
-        s->P32.plane = o.precision != CBS_FP64 && plane_ok<float>(s->P32) && std::getenv("CBS_PLANE") != nullptr;
+        // CBS_PLANE=1 / CBS_NO_PLANE=1 force the plane kernels on (where they exist) / off
+        s->P32.plane = o.precision != CBS_FP64 && std::getenv("CBS_NO_PLANE") == nullptr &&
+                       (std::getenv("CBS_PLANE") != nullptr ? plane_ok<float>(s->P32) : plane_preferred<float>(s->P32));
         const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)),
                                 std::max(grid_for(n), plane_blocks<float>(s->P32)));
         s->npart = nb;

@@ -67,12 +67,20 @@ template <typename R> struct Plan {
     bool plane = false;    // the Born iteration uses the x-y plane kernels (see plane_ok)
 };
 
-// x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane
+// x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane.
+// The Born iteration uses them for planes of at most 4096 values: measured on GB300, 64^3 takes 34.1
+// instead of 40.6 us per iteration, while 128 x 128 planes (64 KiB half-planes, two CTAs per SM) take
+// 212 instead of 157 us, so larger planes keep the row + strided-axis kernels.
 constexpr int kPlaneCL = 2;
+constexpr long long kPlaneMaxValues = 4096;
 inline bool plane_size(int n) { return n == 32 || n == 64 || n == 128; }
 template <typename R> inline bool plane_ok(const Plan<R>& P)
 {
     return sizeof(R) == 4 && P.d.D == 3 && plane_size(P.d.n0) && plane_size(P.d.n1);
+}
+template <typename R> inline bool plane_preferred(const Plan<R>& P)
+{
+    return plane_ok<R>(P) && (long long)P.d.n0 * P.d.n1 <= kPlaneMaxValues;
 }
 template <typename R> inline int plane_blocks(const Plan<R>& P) { return (P.d.D + 1) * P.d.n2 * kPlaneCL; }
 

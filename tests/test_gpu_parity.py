@@ -352,10 +352,10 @@ def test_last_axis_tile_kernel_matches_register_kernel_and_oracle(shape, adjoint
     time) does the same arithmetic in the same order as the all-in-registers kernel: float32 Born
     iterations agree to float32 rounding (contraction into FMAs may differ), and both match the float64
     oracle."""
+    monkeypatch.setenv("CBS_TILE_LAST", "1")
     _, s, P = make(shape, seed=40, precision="fp32")
-    monkeypatch.setenv("CBS_NO_TILE_LAST", "1")
+    monkeypatch.delenv("CBS_TILE_LAST")
     _, s_reg, _ = make(shape, seed=40, precision="fp32")
-    monkeypatch.delenv("CBS_NO_TILE_LAST")
     y = P.scale_source(W.random_source(shape, 41), adjoint)
     x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
     x_reg = torch.zeros_like(x)
@@ -375,7 +375,9 @@ def test_plane_kernels_match_row_axis_kernels_and_oracle(shape, adjoint, monkeyp
     monkeypatch.setenv("CBS_PLANE", "1")
     _, s, P = make(shape, seed=42, precision="fp32")
     monkeypatch.delenv("CBS_PLANE")
+    monkeypatch.setenv("CBS_NO_PLANE", "1")
     _, s_ref, _ = make(shape, seed=42, precision="fp32")
+    monkeypatch.delenv("CBS_NO_PLANE")
     y = P.scale_source(W.random_source(shape, 43), adjoint)
     x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
     x_ref = torch.zeros_like(x)
@@ -396,7 +398,9 @@ def test_plane_kernels_solve_sphere_128(monkeypatch):
     monkeypatch.setenv("CBS_PLANE", "1")
     s = cbs.solver_create(*args, precision="fp32_refine", tol=1e-6, check_every=50)
     monkeypatch.delenv("CBS_PLANE")
+    monkeypatch.setenv("CBS_NO_PLANE", "1")
     s_ref = cbs.solver_create(*args, precision="fp32_refine", tol=1e-6, check_every=50)
+    monkeypatch.delenv("CBS_NO_PLANE")
     s64 = cbs.solver_create(*args, precision="fp64", tol=1e-6)
     f = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
     f_ref = torch.zeros_like(f)
