@@ -996,7 +996,11 @@ void set_l2_window(cbs_solver* s, void* base, size_t bytes)
     cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
     cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
     if (max_persist <= 0 || max_window <= 0) return;
-    const size_t win = std::min(bytes, (size_t)max_window);
+    // Only a field that fits in the persisting carve-out gets a window.  A window over a larger field
+    // marks most of its accesses streaming (evict first) and measured 1.7-1.9x slower per iteration
+    // on GB300 at 256^3 and 512^3; at 128^3 (67 MB) the window makes an iteration 7 % faster.
+    if (bytes > (size_t)max_persist || bytes > (size_t)max_window) return;
+    const size_t win = bytes;
     size_t cur = 0;
     cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
     if (cur < std::min(win, (size_t)max_persist)) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(win, (size_t)max_persist));
