@@ -328,17 +328,18 @@ __device__ __forceinline__ void pass_exchange(CT (&v)[R], CT* sm, int ss, int ti
 
 // Full transform.  On entry v[s] holds position tid + T*slot_q<N,R,0>(s); on
 // exit v[s] holds position tid + T*slot_q<N,R,npass>(s).
-template <int N, int R, int S, bool PAD = false, int P = 0, typename CT, typename Sync>
+// USE_TC = false reads every twiddle from the table (for kernels with no registers to spare).
+template <int N, int R, int S, bool PAD = false, int P = 0, bool USE_TC = true, typename CT, typename Sync>
 __device__ __forceinline__ void fft_run(CT (&v)[R], CT* sm, int ss, int tid, const CT* __restrict__ tw,
                                         const TwCache<N, R, CT>& tc, Sync sync)
 {
     constexpr int T = N / R;
     constexpr int np = plan_npass(N, R);
     static_assert(np > 0, "unsupported FFT size / register split");
-    pass_compute<N, R, T, P, S>(v, tid, tw, tc);
+    pass_compute<N, R, T, P, S, USE_TC>(v, tid, tw, tc);
     if constexpr (P + 1 < np) {
         pass_exchange<N, R, T, P, PAD>(v, sm, ss, tid, sync);
-        fft_run<N, R, S, PAD, P + 1>(v, sm, ss, tid, tw, tc, sync);
+        fft_run<N, R, S, PAD, P + 1, USE_TC>(v, sm, ss, tid, tw, tc, sync);
     }
 }
 

@@ -180,8 +180,7 @@ k_plane_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restr
     R s0 = (R)0, s1 = (R)0;
     {
         const int lr = threadIdx.x / TX, t = threadIdx.x % TX;
-        TwCache<NX, RX, CT> tc;
-        tw_load<NX, RX, TX>(tc, t, twx);
+        const TwCache<NX, RX, CT> tc{};  // twiddles from the table: the prefetched update operands need the registers
         constexpr int np = plan_npass(NX, RX);
 #pragma unroll 1
         for (int b = 0; b < Cfg::ROWS_OWN / Cfg::RB; ++b) {
@@ -202,7 +201,7 @@ k_plane_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restr
                 xv[s] = x[fbase + i0];
                 bv[s] = born_B(M, rb, i0, adj != 0);
             }
-            fft_run<NX, RX, +1, true>(v, row, 1, t, twx, tc, RowSync<TX>());
+            fft_run<NX, RX, +1, true, 0, false>(v, row, 1, t, twx, tc, RowSync<TX>());
 #pragma unroll
             for (int s = 0; s < RX; ++s) {
                 const CT del = cscale(cmul(bv[s], csub(v[s], xv[s])), nu);
