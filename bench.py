@@ -118,17 +118,23 @@ def reduce_over_ranks(local_ms: float, local_units: float, device=None):
 
 
 # ------------------------------------------------------------------ oracle arm
-def cpu_oracle_rate(problem, n_iter=1):
-    """Voxel-iterations/s of the FP64 CPU oracle on the host cores (bounded sample)."""
+def cpu_oracle_rate(problem, min_seconds=10.0, max_iter=200):
+    """Voxel-iterations/s of the FP64 CPU oracle on the host cores, over a bounded sample: FP64 Born
+    iterations of the same workload until at least min_seconds of CPU time (at most max_iter).
+    Returns (rate, seconds, iterations, threads)."""
     from oracle import oracle as O
 
     P = O.Problem(problem.c0, problem.rho, problem.alpha, problem.dx, problem.omega, problem.nabs,
                   problem.gamma_max)
     y = P.scale_source(problem.source)
-    t0 = time.perf_counter()
-    P.iterate(y, n_iter=n_iter, nu=0.8)
-    dt = time.perf_counter() - t0
-    return problem.n_voxels * n_iter / dt, dt, O.max_threads()
+    n, dt = 0, 0.0
+    while n == 0 or (dt < min_seconds and n < max_iter):
+        k = 1 if n == 0 else max(1, min(max_iter - n, int(np.ceil((min_seconds - dt) / (dt / n)))))
+        t0 = time.perf_counter()
+        P.iterate(y, n_iter=k, nu=0.8)
+        dt += time.perf_counter() - t0
+        n += k
+    return problem.n_voxels * n / dt, dt, n, O.max_threads()
 
 
 def run_reference(args):
@@ -140,14 +146,16 @@ def run_reference(args):
     p = W.sphere_128()
     rates = []
     for _ in range(args.warmup):
-        cpu_oracle_rate(p, 1)
-    t_all = 0.0
+        cpu_oracle_rate(p, min_seconds=0.0)
+    t_all, n_all = 0.0, 0
     for _ in range(args.steps):
-        r, dt, cores = cpu_oracle_rate(p, 1)
+        r, dt, n, cores = cpu_oracle_rate(p, min_seconds=5.0)
         rates.append(r)
         t_all += dt
-    value = float(p.n_voxels * args.steps / t_all)
-    sample = f"{args.steps} x 1 FP64 Born iteration of the 128^3 sphere workload (own FFT, OpenMP)"
+        n_all += n
+    value = float(p.n_voxels * n_all / t_all)
+    sample = (f"{args.steps} steps of >= 5 s each: {n_all} FP64 Born iterations of the 128^3 sphere workload "
+              f"(own FFT, OpenMP), {t_all:.1f} s")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -161,7 +169,8 @@ def run_reference(args):
 # -------------------------------------------------------------------- GPU arm
 # DRAM read + write bytes per launch of each float32 iteration kernel on the 128^3 workload, from one
 # `ncu --set full` capture of the current kernels (null the entry when its kernel changes)
-NCU_TRAFFIC_128 = {"rows_fwd": 217.21e6, "last_symbol": 74.94e6, "rows_inv": 206.63e6}
+NCU_TRAFFIC_128 = {"rows_fwd": 180.34e6, "axis_fwd": 67.98e6, "last_symbol": 68.07e6, "axis_inv": 68.11e6,
+                   "rows_inv": 217.05e6}
 
 
 def kernel_bytes_per_voxel(D=3, fp=4):
@@ -294,9 +303,9 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, dt, cores = cpu_oracle_rate(p, 1)
+        rate, dt, n_cpu, cores = cpu_oracle_rate(p, min_seconds=10.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"1 FP64 Born iteration of the same 128^3 workload ({dt:.1f} s)"}
+               "sample": f"{n_cpu} FP64 Born iterations of the same 128^3 workload ({dt:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
