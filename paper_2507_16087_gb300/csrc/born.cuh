@@ -386,8 +386,10 @@ __device__ __forceinline__ void apply_symbol(const Symbol<R>& Sy, int mode, cons
     }
 }
 
+// two blocks an SM when a block has fewer than 512 threads; with 512 (the 1024- and 2048-point and 512-point
+// 8-column tiles) the C transforms keep their registers (a 64-register cap spilled them) at one block an SM
 template <typename R, int NL, int RL, int COLS, int C>
-__global__ void __launch_bounds__((NL / RL) * COLS, 2)
+__global__ void __launch_bounds__((NL / RL) * COLS, ((NL / RL) * COLS >= 512) ? 1 : 2)
 k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int mode)
 {
     using CT = cplx<R>;
