@@ -37,6 +37,7 @@
 #ifndef CBS_H
 #define CBS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -73,6 +74,15 @@ typedef struct {
     double power;
 } cbs_boundary;
 
+/* Optional device allocator for the solver's own arrays, so that a framework's caching allocator (torch's,
+ * for instance) can serve them instead of cudaMalloc / cudaFree.  dev_alloc(bytes, stream, ctx) gets
+ * options.stream as `stream` and returns device memory aligned to at least 256 bytes (the staged bulk
+ * and tensor copies need 16), or NULL on failure; dev_free(ptr, ctx) takes back what dev_alloc gave.
+ * The solver calls them from solver_create (its arrays and set-up temporaries) and solver_destroy, on the
+ * calling thread, after its own work on the memory is complete.  The paper has no counterpart. */
+typedef void* (*cbs_dev_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*cbs_dev_free_fn)(void* ptr, void* ctx);
+
 typedef struct {
     int precision;     /* CBS_FP64 (default), CBS_FP32_REFINE, CBS_FP32 */
     double nu;         /* 0 < nu < 1 (eq. BornAlt); 0 -> 0.8 */
@@ -88,6 +98,9 @@ typedef struct {
     int grid_kind;     /* CBS_GRID_STAGGERED (default, App. B.1: velocity at x + dx/2 e_eta, staggered
                           density, symbol i k e^{i k dx/2}) or CBS_GRID_COLLOCATED (App. B: velocity at
                           the cell centres, unshifted density and gamma, symbol i k) */
+    cbs_dev_alloc_fn dev_alloc;  /* NULL (default): cudaMalloc; else set dev_free too (CBS_EINVAL otherwise) */
+    cbs_dev_free_fn dev_free;
+    void* alloc_ctx;             /* passed to dev_alloc / dev_free */
 } cbs_options;
 
 typedef struct {

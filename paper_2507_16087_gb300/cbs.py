@@ -31,11 +31,16 @@ class cbs_boundary(ctypes.Structure):
     _fields_ = [("n_abs", (ctypes.c_int * 2) * 3), ("gamma_max", ctypes.c_double), ("power", ctypes.c_double)]
 
 
+DEV_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+DEV_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class cbs_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("shift_rule", ctypes.c_int), ("tol", ctypes.c_double), ("tol_inner", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("grid_kind", ctypes.c_int)]
+                ("grid_kind", ctypes.c_int), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p)]
 
 
 class cbs_info(ctypes.Structure):
@@ -149,8 +154,9 @@ def _check_field(t, shape):
 def solver_create(c0, rho, alpha, dx: float, omega: float, nabs, gamma_max: float, power: float = 2.0,
                   precision="fp64", nu: float = 0.8, beta: float = 0.95, shift_rule: int = CBS_SHIFT_MIDRANGE,
                   tol: float = 1e-6, tol_inner: float = 1e-4, max_iter: int = 100000, check_every: int = 50,
-                  stream=None, collocated: bool = False):
-    """c0, rho, alpha: cuda float64 tensors of the grid shape (n[D-1], ..., n[0])."""
+                  stream=None, collocated: bool = False, allocator=None):
+    """c0, rho, alpha: cuda float64 tensors of the grid shape (n[D-1], ..., n[0]).  allocator="torch" serves
+    the solver's device arrays from torch's caching allocator (on `stream`) instead of cudaMalloc."""
     import torch
     lib = load()
     for t in (c0, rho, alpha):
@@ -173,12 +179,38 @@ def solver_create(c0, rho, alpha, dx: float, omega: float, nabs, gamma_max: floa
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = ctypes.c_void_p(int(stream.cuda_stream))
+    callbacks = None
+    if allocator == "torch":
+        callbacks = _torch_allocator(stream)
+        o.dev_alloc, o.dev_free = callbacks
+    elif allocator is not None:
+        raise ValueError("allocator must be None or 'torch'")
     h = ctypes.c_void_p()
     st = lib.solver_create(ctypes.byref(g), float(dx), float(omega), _ptr(c0), _ptr(rho), _ptr(alpha),
                            ctypes.byref(b), ctypes.byref(o), ctypes.byref(h))
     if st != CBS_OK:
         raise CBSError(st, lib.cbs_last_error(None).decode())
-    return Solver(h, tuple(c0.shape), o)
+    sv = Solver(h, tuple(c0.shape), o)
+    sv._callbacks = callbacks  # the C side calls them until solver_destroy
+    return sv
+
+
+def _torch_allocator(stream):
+    """dev_alloc / dev_free callbacks over torch's caching allocator, blocks associated with `stream`."""
+    import torch
+
+    dev = stream.device
+
+    def alloc(nbytes, _stream, _ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=stream)
+        except RuntimeError:  # out of memory: the solver reports CBS_ENOMEM
+            return None
+
+    def free(ptr, _ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return DEV_ALLOC_FN(alloc), DEV_FREE_FN(free)
 
 
 class Solver:
@@ -190,6 +222,7 @@ class Solver:
         self.ndim = len(shape)
         self.ncomp = self.ndim + 1
         self.options = options
+        self._callbacks = None
         self._lib = load()
 
     @property

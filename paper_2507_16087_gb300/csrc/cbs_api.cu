@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <type_traits>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -479,15 +480,36 @@ struct CudaError {
     int line;
 };
 
-template <typename T> T* dalloc(cbs_solver* s, size_t count)
+// device memory from the caller's allocator (options.dev_alloc) or cudaMalloc
+void* dev_get(cbs_solver* s, size_t bytes)
 {
     void* p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
+    if (s->opt.dev_alloc) {
+        p = s->opt.dev_alloc(bytes, s->opt.stream, s->opt.alloc_ctx);
+        if (!p) throw Fail{CBS_ENOMEM};
+        if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+            s->opt.dev_free(p, s->opt.alloc_ctx);
+            throw Fail{CBS_EINVAL};
+        }
+        return p;
+    }
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         throw Fail{CBS_ENOMEM};
     }
+    return p;
+}
+
+void dev_put(cbs_solver* s, void* p)
+{
+    if (s->opt.dev_free) s->opt.dev_free(p, s->opt.alloc_ctx);
+    else cudaFree(p);
+}
+
+template <typename T> T* dalloc(cbs_solver* s, size_t count)
+{
+    if (count == 0) count = 1;
+    void* p = dev_get(s, count * sizeof(T));
     s->allocs.push_back(p);
     return static_cast<T*>(p);
 }
@@ -498,7 +520,7 @@ void dfree(cbs_solver* s, void* p)
     auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
     if (it != s->allocs.end()) {
         cudaStreamSynchronize(s->st);
-        cudaFree(p);
+        dev_put(s, p);
         s->allocs.erase(it);
     }
 }
@@ -1144,7 +1166,7 @@ void solver_destroy(cbs_solver* s)
         if (s->graph64[a]) cudaGraphExecDestroy(s->graph64[a]);
         if (s->graph32[a]) cudaGraphExecDestroy(s->graph32[a]);
     }
-    for (void* p : s->allocs) cudaFree(p);
+    for (void* p : s->allocs) dev_put(s, p);
     if (s->host_red) cudaFreeHost(s->host_red);
     if (s->ev_user) cudaEventDestroy(s->ev_user);
     if (s->ev0) cudaEventDestroy(s->ev0);
@@ -1179,6 +1201,8 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         return set_err(nullptr, CBS_EINVAL, "bad grid kind");
     if (o.shift_rule != CBS_SHIFT_MIDRANGE && o.shift_rule != CBS_SHIFT_MEDIAN && o.shift_rule != CBS_SHIFT_MEC)
         return set_err(nullptr, CBS_EINVAL, "bad shift rule");
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
+        return set_err(nullptr, CBS_EINVAL, "dev_alloc and dev_free must be set together");
     cbs_boundary b{};
     if (boundary) b = *boundary;
     if (b.power == 0) b.power = 2.0;
@@ -1379,7 +1403,8 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         return set_err(nullptr, CBS_ECUDA, msg);
     } catch (const Fail& f) {
         solver_destroy(s);
-        return set_err(nullptr, f.code, "device allocation failed");
+        return set_err(nullptr, f.code, f.code == CBS_EINVAL ? "dev_alloc returned memory not aligned to 256 bytes"
+                                                             : "device allocation failed");
     }
     *out = s;
     return CBS_OK;

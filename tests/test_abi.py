@@ -71,3 +71,41 @@ def test_oracle_shares_nothing_with_the_cuda_path():
             src = open(os.path.join(ROOT, "oracle", f)).read()
             assert "csrc" not in src and "import cbs" not in src and "libcbs_gb300" not in src, f
             assert "paper_2507_16087_gb300" not in src, f
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the header's size and field offsets (compiled with gcc)."""
+    structs = {"cbs_grid": cbs.cbs_grid, "cbs_boundary": cbs.cbs_boundary, "cbs_options": cbs.cbs_options,
+               "cbs_info": cbs.cbs_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cbs.h"', "int main(void) {"]
+    for name, ct in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in ct._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(ln.rsplit(" ", 1) for ln in out.splitlines())
+    for name, ct in structs.items():
+        assert int(got[name]) == ctypes.sizeof(ct), name
+        for fname, _ in ct._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(ct, fname).offset, (name, fname)
+
+
+def test_allocator_callbacks_must_come_in_pairs():
+    """solver_create rejects a dev_alloc without dev_free before touching the device (CPU-only check)."""
+    lib = cbs.load()
+    g = cbs.cbs_grid()
+    g.ndim = 2
+    g.n[0], g.n[1] = 16, 16
+    o = cbs.cbs_options()
+    o.dev_alloc = cbs.DEV_ALLOC_FN(lambda nbytes, stream, ctx: None)
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the options are checked first
+    st = lib.solver_create(ctypes.byref(g), 1e-3, 1e6, dummy, dummy, dummy, None, ctypes.byref(o), ctypes.byref(h))
+    assert st == cbs.CBS_EINVAL
+    assert b"dev_alloc and dev_free" in lib.cbs_last_error(None)
+    assert not h.value

@@ -410,3 +410,32 @@ def test_plane_kernels_solve_sphere_128(monkeypatch):
     assert s64.residual_norm(f, T(p.source)) <= 1.01e-6
     assert abs(info["iters"] - info_ref["iters"]) <= 100
     assert rel(f.cpu().numpy(), f_ref.cpu().numpy()) <= 1e-4
+
+
+def test_torch_caching_allocator_serves_solver_memory():
+    """allocator='torch': the solver's arrays come from torch's caching allocator (counted by
+    torch.cuda.memory_allocated while the solver lives, returned on destroy) and the solve is bitwise the
+    same as with cudaMalloc."""
+    cbs = _cbs()
+    shape = (16, 24, 32)
+    p = W.smooth_random_medium(shape, seed=50, n_abs=3)
+    args = (T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max)
+    src = T(W.random_source(shape, 51))
+    f_t = torch.zeros((4,) + shape, dtype=torch.complex128, device=DEV)
+    f_c = torch.zeros_like(f_t)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    s_t = cbs.solver_create(*args, precision="fp32_refine", tol=1e-8, allocator="torch")
+    held = torch.cuda.memory_allocated() - base
+    n = 4 * int(np.prod(shape))
+    assert held >= n * (3 * 16 + 3 * 8)  # x, y, w in float64 and float32 at least
+    s_c = cbs.solver_create(*args, precision="fp32_refine", tol=1e-8)
+    assert torch.cuda.memory_allocated() - base == held  # cudaMalloc memory is not torch's
+    i_t = s_t.solve_forward(src, f_t)
+    i_c = s_c.solve_forward(src, f_c)
+    assert i_t["iters"] == i_c["iters"] and i_t["rel_residual"] <= 1e-8
+    assert torch.equal(f_t, f_c)
+    s_t.destroy()
+    s_c.destroy()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
