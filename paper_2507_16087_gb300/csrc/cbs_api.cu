@@ -830,7 +830,8 @@ template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* 
 }
 
 // FP32 inner Born iterations with FP64 residual, norm and correction
-cbs_status solve_refine(cbs_solver* s, bool adj, cbs_info* info)
+// zero_start: x64 = 0 on entry, so the first residual is y itself (no float64 operator apply)
+cbs_status solve_refine(cbs_solver* s, bool adj, cbs_info* info, bool zero_start)
 {
     const long long n = field_len(s);
     double ny2;
@@ -844,10 +845,15 @@ cbs_status solve_refine(cbs_solver* s, bool adj, cbs_info* info)
     const int maxit = s->opt.max_iter;
     // r = y - A_s x in float64 (into w64)
     double r[2];
-    apply_operator<double>(s, adj, INV_RESID);
-    read_red(s, r);
-    info->residual_checks++;
-    double rn2 = r[0];
+    double rn2 = ny2;
+    if (zero_start) {
+        CUDA_TRY(cudaMemcpyAsync(s->w64, s->y64, n * sizeof(double2), cudaMemcpyDeviceToDevice, s->st));
+    } else {
+        apply_operator<double>(s, adj, INV_RESID);
+        read_red(s, r);
+        info->residual_checks++;
+        rn2 = r[0];
+    }
     double rel = std::sqrt(rn2 / ny2), inc = 0.0;
     int it = 0, outer = 0;
     cbs_status st = CBS_OK;
@@ -903,7 +909,7 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
         CUDA_TRY(cudaEventRecord(s->ev0, s->st));
         prepare(s, src, x0, adj);
         cbs_status st;
-        if (s->opt.precision == CBS_FP32_REFINE) st = solve_refine(s, adj, &info);
+        if (s->opt.precision == CBS_FP32_REFINE) st = solve_refine(s, adj, &info, x0 == nullptr);
         else if (s->opt.precision == CBS_FP32) st = solve_plain<float>(s, adj, &info);
         else st = solve_plain<double>(s, adj, &info);
         finish_field(s, field);
