@@ -263,6 +263,25 @@ def run_gpu(args):
     kt = s.time_kernels(y, x, 5)
     kt = s.time_kernels(y, x, 20)
     s.destroy()
+    # the cuFFT comparison build of the same iteration (timed only), beside the fused iteration replayed from
+    # its captured graphs as a solve runs it
+    s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision="fp32_refine", **kw)
+    x.zero_()
+    s.cufft_iterate(y, x, 3)
+    cufft_ms = s.cufft_iterate(y, x, 20)
+    x.zero_()
+    s.born_iterate(y, x, 50)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.born_iterate(y, x, 200)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    own_ms = e0.elapsed_time(e1) / 200
+    s.destroy()
+    cufft = {"iteration_ms": cufft_ms, "voxel_iters_per_s": Nv / (cufft_ms / 1e3), "own_iteration_ms": own_ms,
+             "own_voxel_iters_per_s": Nv / (own_ms / 1e3), "speedup_vs_cufft": cufft_ms / own_ms,
+             "what": "same float32 iteration: cuFFT batched C2C plans + plain pointwise kernels (stream launches)"}
     bpv = kernel_bytes_per_voxel(3, 4)
     peak, peak_kind = _peaks()
     top = max((k for k in kt if bpv.get(k, 0) > 0), key=lambda k: kt[k])
@@ -316,7 +335,7 @@ def run_gpu(args):
                 "time_to_1e-6_ms": step_ms, "iters": float(np.mean(iters)),
                 "outer_iters": infos[-1]["outer_iters"], "rel_residual": infos[-1]["rel_residual"],
                 "setup_ms": infos[-1]["t_setup_ms"], "fp64": fp64, "roofline": roof, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "serving": serving}
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "serving": serving, "cufft_baseline": cufft}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist

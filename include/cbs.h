@@ -219,6 +219,14 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
 cbs_status green_apply_noalloc(const cbs_grid* grid, double dx, const double* scalars, const void* in, void* out,
                                int adjoint, void* stream);
 
+/* Comparison build of the iteration (timed only; the solver never calls it): n_iter float32 Born
+ * iterations of eq. BornAlt with the App. B.1 symbol, the transforms done by cuFFT (batched
+ * complex-to-complex plans over the C components, made on first use and kept by the solver) and the
+ * rest by plain pointwise kernels: w = B x + y, FFT, symbol, IFFT, x += nu B (w - x).  y: scaled source,
+ * x: scaled iterate, updated in place (device complex128 [C][N], as born_iterate).  *ms_per_iter: CUDA-event
+ * time per iteration on the solver's stream, casts excluded.  CBS_EINVAL for a float64 solver. */
+cbs_status cufft_baseline_iterate(cbs_solver* s, const void* y, void* x, int n_iter, int adjoint, double* ms_per_iter);
+
 /* Failure-detection self-test (no counterpart in the paper).  which =
  * CBS_SELFTEST_BULK_TIMEOUT launches one block whose bulk copy delivers half
  * the bytes its shared-memory barrier expects, so the barrier never completes:

@@ -60,7 +60,8 @@ class cbs_info(ctypes.Structure):
 
 EXPORTS = ("solver_create", "solve_forward", "solve_adjoint", "residual_norm", "born_iterate", "green_apply",
            "operator_apply", "scale_source", "unscale_field", "solver_scalars", "solver_time_kernels",
-           "solver_destroy", "cbs_last_error", "green_apply_noalloc", "medium_gradient", "cbs_selftest")
+           "solver_destroy", "cbs_last_error", "green_apply_noalloc", "medium_gradient", "cbs_selftest",
+           "cufft_baseline_iterate")
 
 _lock = threading.Lock()
 _lib = None
@@ -116,6 +117,8 @@ def load(path: str | None = None):
         lib.green_apply_noalloc.argtypes = [ctypes.POINTER(cbs_grid), D, ctypes.POINTER(D), V, V, I, V]
         lib.cbs_selftest.restype = S
         lib.cbs_selftest.argtypes = [I, ctypes.POINTER(I)]
+        lib.cufft_baseline_iterate.restype = S
+        lib.cufft_baseline_iterate.argtypes = [V, V, V, I, I, ctypes.POINTER(D)]
         if path is None:
             _lib = lib
         return lib
@@ -328,6 +331,16 @@ class Solver:
             self._raise(st)
         return {"a1": complex(out[0], out[1]), "a2": complex(out[2], out[3]), "lambda1": out[4],
                 "lambda2": out[5]}
+
+    def cufft_iterate(self, y, x, n_iter: int, adjoint=False) -> float:
+        """The cuFFT comparison build of n_iter float32 iterations (x updated in place); ms per iteration."""
+        _check_field(y, self.field_shape)
+        _check_field(x, self.field_shape)
+        ms = ctypes.c_double()
+        st = self._lib.cufft_baseline_iterate(self._h, _ptr(y), _ptr(x), int(n_iter), int(adjoint), ctypes.byref(ms))
+        if st != CBS_OK:
+            self._raise(st)
+        return ms.value
 
     def time_kernels(self, y, x, n_iter: int):
         _check_field(y, self.field_shape)

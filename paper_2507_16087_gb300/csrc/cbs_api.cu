@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -19,6 +20,7 @@
 
 #include "cbs.h"
 #include "launch.cuh"
+#include "baseline_cufft.cuh"
 
 namespace cbs {
 CBS_EXTERN_LAUNCHERS(float)
@@ -427,6 +429,8 @@ struct cbs_solver {
     cudaEvent_t ev_user = nullptr, ev0 = nullptr, ev1 = nullptr;
     std::string err = "no error";
     std::vector<void*> allocs;
+    cufftHandle fft_plan = 0;  // comparison baseline only (cufft_baseline_iterate), made on first use
+    bool fft_plan_ok = false;
 
     double *rs64[3] = {}, *kp64 = nullptr, *et64 = nullptr;
     float *rs32[3] = {}, *kp32 = nullptr, *et32 = nullptr;
@@ -1172,6 +1176,7 @@ void solver_destroy(cbs_solver* s)
         if (s->graph64[a]) cudaGraphExecDestroy(s->graph64[a]);
         if (s->graph32[a]) cudaGraphExecDestroy(s->graph32[a]);
     }
+    if (s->fft_plan_ok) cufftDestroy(s->fft_plan);
     for (void* p : s->allocs) dev_put(s, p);
     if (s->host_red) cudaFreeHost(s->host_red);
     if (s->ev_user) cudaEventDestroy(s->ev_user);
@@ -1693,6 +1698,58 @@ cbs_status cbs_selftest(int which, int* result)
     if (e != cudaSuccess) return CBS_ECUDA;
     *result = (h[0] == kErrBulkTimeout && h[1] == 1) ? CBS_ETIMEOUT : CBS_OK;
     return CBS_OK;
+}
+
+cbs_status cufft_baseline_iterate(cbs_solver* s, const void* y, void* x, int n_iter, int adjoint, double* ms_per_iter)
+{
+    if (!s) return CBS_EINVAL;
+    if (!y || !x || n_iter <= 0 || !ms_per_iter) return set_err(s, CBS_EINVAL, "bad argument");
+    if (s->opt.precision == CBS_FP64)
+        return set_err(s, CBS_EINVAL, "the cuFFT baseline runs the float32 iteration: create the solver in float32");
+    try {
+        begin_call(s);
+        const long long n = field_len(s);
+        if (!s->fft_plan_ok) {
+            int dims[3] = {s->n[2], s->n[1], s->n[0]};  // slowest axis first
+            int* d0 = s->D == 3 ? dims : dims + 1;
+            if (cufftPlanMany(&s->fft_plan, s->D, d0, nullptr, 1, (int)s->N, nullptr, 1, (int)s->N, CUFFT_C2C, s->C) !=
+                CUFFT_SUCCESS)
+                return set_err(s, CBS_ECUDA, "cufftPlanMany failed");
+            s->fft_plan_ok = true;
+        }
+        if (cufftSetStream(s->fft_plan, s->st) != CUFFT_SUCCESS) return set_err(s, CBS_ECUDA, "cufftSetStream failed");
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)y, s->y32, 1.0, n);
+        k_cast_64_32<<<grid_for(n), 256, 0, s->st>>>((const double2*)x, s->x32, 1.0, n);
+        CUDA_TRY(cudaGetLastError());
+        Plan<float>& P = s->P32;
+        const int g = grid_for(n), gs = grid_for(s->N);
+        const int mode = adjoint ? SYM_GREEN_ADJ : SYM_GREEN;
+        cufftComplex* w = reinterpret_cast<cufftComplex*>(s->w32);
+        CUDA_TRY(cudaEventRecord(s->ev0, s->st));
+        for (int it = 0; it < n_iter; ++it) {
+            k_base_pre<float><<<g, 256, 0, s->st>>>(P.d, P.M, s->x32, s->y32, s->w32, adjoint);
+            CUDA_TRY(cudaGetLastError());
+            if (cufftExecC2C(s->fft_plan, w, w, CUFFT_FORWARD) != CUFFT_SUCCESS)
+                return set_err(s, CBS_ECUDA, "cufftExecC2C failed");
+            if (s->D == 3) k_base_symbol<float, 4><<<gs, 256, 0, s->st>>>(P.d, P.Sy, s->w32, mode);
+            else k_base_symbol<float, 3><<<gs, 256, 0, s->st>>>(P.d, P.Sy, s->w32, mode);
+            CUDA_TRY(cudaGetLastError());
+            if (cufftExecC2C(s->fft_plan, w, w, CUFFT_INVERSE) != CUFFT_SUCCESS)
+                return set_err(s, CBS_ECUDA, "cufftExecC2C failed");
+            k_base_update<float><<<g, 256, 0, s->st>>>(P.d, P.M, s->x32, s->w32, adjoint, (float)s->opt.nu, s->partials);
+            CUDA_TRY(cudaGetLastError());
+        }
+        CUDA_TRY(cudaEventRecord(s->ev1, s->st));
+        k_cast_32_64<<<grid_for(n), 256, 0, s->st>>>(s->x32, (double2*)x, n);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(s->st));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+        *ms_per_iter = ms / n_iter;
+        return CBS_OK;
+    } catch (const CudaError& e) {
+        return set_err(s, CBS_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e.e) + " in " + e.what);
+    }
 }
 
 }  // extern "C"

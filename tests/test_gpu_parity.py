@@ -439,3 +439,20 @@ def test_torch_caching_allocator_serves_solver_memory():
     s_c.destroy()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == base
+
+
+@pytest.mark.parametrize("shape", [(16, 24, 32), (64, 64, 64), (96, 128)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_cufft_baseline_matches_fused_kernels_and_oracle(shape, adjoint):
+    """The cuFFT comparison build runs the same float32 iteration: it matches the fused kernels to float32
+    rounding and the float64 oracle to the float32 tolerance."""
+    _, s, P = make(shape, seed=44, precision="fp32")
+    y = P.scale_source(W.random_source(shape, 45), adjoint)
+    x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    x_ref = torch.zeros_like(x)
+    ms = s.cufft_iterate(T(y), x, 10, adjoint)
+    assert ms > 0
+    s.born_iterate(T(y), x_ref, 10, adjoint)
+    assert rel(x.cpu().numpy(), x_ref.cpu().numpy()) <= 2e-6
+    xr, _ = P.iterate(y, n_iter=10, nu=0.5, adjoint=adjoint)
+    assert rel(x.cpu().numpy(), xr) <= 1e-5
