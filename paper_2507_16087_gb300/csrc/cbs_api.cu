@@ -778,6 +778,17 @@ void finish_field(cbs_solver* s, void* field)
 bool finite(double v) { return std::isfinite(v); }
 
 // plain FP64 (or plain FP32) solve on the scaled variables; x64/y64 prepared
+// Skips residual checks that cannot stop the iteration yet.  For the stationary Born iteration the
+// residual and the increment ||x_{k+1} - x_k|| / ||x_{k+1}|| decay together once the slowest mode
+// dominates, so after a check has measured the ratio residual / increment, a block whose increment
+// predicts a residual above twice the target skips the check (an operator apply and a host round trip).
+// A wrong prediction costs iterations, never accuracy: the loop stops only on a measured residual.
+struct ResidualGate {
+    double ratio = -1.0;
+    bool skip(double inc, double target) const { return ratio > 0 && inc > 0 && inc * ratio > 2.0 * target; }
+    void learn(double res, double inc) { ratio = (inc > 0 && res > 0) ? res / inc : -1.0; }
+};
+
 template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* info)
 {
     const long long n = field_len(s);
@@ -802,11 +813,13 @@ template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* 
     int it = 0;
     double rel = 1.0, inc = 0.0;
     cbs_status st = CBS_OK;
+    ResidualGate gate;
     while (it < maxit) {
         const int blk = std::min(s->opt.check_every, maxit - it);
         run_iterations<R>(s, blk, adj);
         it += blk;
         inc = read_last_increment(s);
+        if (tol > 0 && finite(inc) && gate.skip(inc, tol) && it < maxit) continue;
         if (tol > 0) {
             apply_operator<R>(s, adj, INV_RESID);
             double r[2];
@@ -814,6 +827,7 @@ template <typename R> cbs_status solve_plain(cbs_solver* s, bool adj, cbs_info* 
             info->residual_checks++;
             rel = std::sqrt(r[0] / r[1]);
             if (!finite(rel) || !finite(inc)) { st = CBS_EDIVERGED; break; }
+            gate.learn(rel, inc);
             if (rel <= tol) break;
         } else if (!finite(inc)) {
             st = CBS_EDIVERGED;
@@ -869,16 +883,20 @@ cbs_status solve_refine(cbs_solver* s, bool adj, cbs_info* info, bool zero_start
         s->launches += 1;
         CUDA_TRY(cudaMemsetAsync(s->x32, 0, n * sizeof(float2), s->st));
         const double target = std::max(s->opt.tol_inner, 0.5 * tol / rel);
+        ResidualGate gate;
         while (it < maxit) {
             const int blk = std::min(s->opt.check_every, maxit - it);
             run_iterations<float>(s, blk, adj);
             it += blk;
             inc = read_last_increment(s);
+            if (!finite(inc)) { st = CBS_EDIVERGED; break; }
+            if (gate.skip(inc, target) && it < maxit) continue;
             apply_operator<float>(s, adj, INV_RESID);  // inner residual (float32)
             double ri[2];
             read_red(s, ri);
             const double rr = std::sqrt(ri[0] / ri[1]);
-            if (!finite(rr) || !finite(inc)) { st = CBS_EDIVERGED; break; }
+            if (!finite(rr)) { st = CBS_EDIVERGED; break; }
+            gate.learn(rr, inc);
             if (rr <= target) break;
         }
         if (st != CBS_OK) break;
