@@ -367,7 +367,7 @@ def test_last_axis_tile_kernel_matches_register_kernel_and_oracle(shape, adjoint
 
 
 @pytest.mark.parametrize("shape", [(16, 32, 32), (12, 32, 64), (24, 64, 32), (8, 128, 64), (16, 128, 128),
-                                   (48, 64, 128)])
+                                   (48, 64, 128), (16, 128, 32), (24, 32, 128)])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_plane_kernels_match_row_axis_kernels_and_oracle(shape, adjoint, monkeypatch):
     """The x-y plane kernels (a CTA pair per (component, z) plane, both transforms on chip) against the
