@@ -797,4 +797,85 @@ k_last_symbol_tile(const __grid_constant__ CUtensorMap tmap, Dims d, Symbol<R> S
     }
 }
 
+// --------------------------------------------- axis_fft, persistent and pipelined
+// The k_axis_fft transform with its column tiles staged by tensor copies: a
+// persistent CTA walks the tiles (blockIdx.x, + gridDim.x, ...) with two
+// shared-memory stages, so the copy of the next tile lands while the current
+// one is transformed.  A tile [NA][COLS] (all y of COLS x-columns at one
+// (component, z)) is one box {COLS, NA, 1} of tmap, which describes the field
+// as {n0, n1, C*n2} 8-byte elements; n0 % COLS == 0.  The transform's exchanges
+// run in the tile's own stage; results go to w with plain stores (each tile is
+// read and written by one CTA, tiles are disjoint).
+template <typename R, int NA, int COLS> struct AxisPipeCfg {
+    static constexpr uint32_t TILE_BYTES = (uint32_t)NA * COLS * sizeof(cplx<R>);
+    static constexpr size_t SMEM = 2 * (size_t)TILE_BYTES + 2 * sizeof(uint64_t);
+};
+
+template <typename R, int NA, int RA, int COLS, int S>
+__global__ void __launch_bounds__(AxisCfg<NA, RA, COLS>::THREADS, 3)
+k_axis_fft_pipe(const __grid_constant__ CUtensorMap tmap, Dims d, cplx<R>* __restrict__ w,
+                const cplx<R>* __restrict__ tw, int* err)
+{
+    using CT = cplx<R>;
+    using Cfg = AxisPipeCfg<R, NA, COLS>;
+    constexpr int T = NA / RA;
+    constexpr int np = plan_npass(NA, RA);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    CT* stage0 = reinterpret_cast<CT*>(smraw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + 2 * (size_t)Cfg::TILE_BYTES);
+    const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    const int xblocks = d.n0 / COLS;
+    const long long ntiles = (long long)(d.D + 1) * d.n2 * xblocks;
+    if (smem_u32(smraw) & 127u) {  // block-uniform; no copy issued
+        if (threadIdx.x == 0) atomicExch(err, kErrTileAlign);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    // thread 0 issues the copy of tile `tile` into stage `st`
+    auto issue = [&](long long tile, int st) {
+        const int xb = (int)(tile % xblocks);
+        const int zc = (int)(tile / xblocks);  // c * n2 + i2
+        mbar_expect_tx(&bar[st], Cfg::TILE_BYTES);
+        tma_load_3d(stage0 + (size_t)st * NA * COLS, &tmap, xb * COLS, 0, zc, &bar[st]);
+    };
+    if (threadIdx.x == 0) {
+        if ((long long)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((long long)blockIdx.x + gridDim.x < ntiles) issue((long long)blockIdx.x + gridDim.x, 1);
+    }
+    TwCache<NA, RA, CT> tc;
+    tw_load<NA, RA, T>(tc, t, tw);
+    uint32_t phases = 0u;  // bit st: parity of stage st's next completion
+    int st = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, st ^= 1) {
+        const uint32_t ph = (phases >> st) & 1u;
+        const bool ok = mbar_wait_bounded(&bar[st], ph);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, kErrBulkTimeout);
+                // let the copies still in flight land before the block leaves
+                mbar_wait_bounded(&bar[st], ph);
+                if (tile + gridDim.x < ntiles) mbar_wait_bounded(&bar[st ^ 1], (phases >> (st ^ 1)) & 1u);
+            }
+            return;
+        }
+        phases ^= 1u << st;
+        CT* sm = stage0 + (size_t)st * NA * COLS;
+        CT v[RA];
+#pragma unroll
+        for (int s = 0; s < RA; ++s) v[s] = sm[(t + T * slot_q<NA, RA, 0>(s)) * COLS + col];
+        fft_run<NA, RA, S>(v, sm + col, COLS, t, tw, tc, BlockSync());
+        const int xb = (int)(tile % xblocks);
+        const long long zc = tile / xblocks;
+        const long long base = zc * (long long)d.n0 * d.n1 + xb * COLS + col;
+#pragma unroll
+        for (int s = 0; s < RA; ++s) w[base + (long long)(t + T * slot_q<NA, RA, np>(s)) * d.n0] = v[s];
+        __syncthreads();  // every thread is done with this stage (inputs and exchanges)
+        if (threadIdx.x == 0 && tile + 2LL * gridDim.x < ntiles) issue(tile + 2LL * gridDim.x, st);
+    }
+}
+
 }  // namespace cbs

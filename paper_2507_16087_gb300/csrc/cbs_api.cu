@@ -1110,6 +1110,38 @@ template <typename R> void fill_tile_map(cbs_solver* s, Plan<R>& P, const void* 
     TRACE("tile map for the last axis: %s", r == CUDA_SUCCESS ? "yes" : "no");
 }
 
+// Tensor-copy descriptor and persistent grid of the pipelined strided-axis kernel (3D float32, n1 <= 256,
+// n0 % COLS == 0): the field as {n0, n1, C*n2} 8-byte elements, box {COLS, n1, 1}.  Opt-in with
+// CBS_AXIS_PIPE=1.
+template <typename R> void fill_axis_map(cbs_solver* s, Plan<R>& P, const void* field)
+{
+    P.axis_field = nullptr;
+    P.axis_grid = 0;
+    const int n1 = s->n[1];
+    if (s->D != 3 || field == nullptr || !axis_pipe_ok<R>(n1) || s->n[0] % cols_axis<R>(n1) != 0) return;
+    if (std::getenv("CBS_AXIS_PIPE") == nullptr) return;
+    auto enc = tensor_map_encoder();
+    if (!enc) return;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const int per_sm = axis_pipe_blocks_per_sm<R>(n1);
+    if (per_sm <= 0) return;
+    const cuuint64_t gdim[3] = {(cuuint64_t)s->n[0], (cuuint64_t)n1, (cuuint64_t)s->C * s->n[2]};
+    const cuuint64_t gstride[2] = {(cuuint64_t)s->n[0] * sizeof(cplx<R>), (cuuint64_t)s->n[0] * n1 * sizeof(cplx<R>)};
+    const cuuint32_t box[3] = {(cuuint32_t)cols_axis<R>(n1), (cuuint32_t)n1, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = enc(&P.tmap_axis, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(field), gdim, gstride,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+    P.axis_field = field;
+    P.axis_grid = sms * per_sm;
+    TRACE("pipelined axis kernel: %d CTAs", P.axis_grid);
+}
+
 template <typename R> void fill_plan(cbs_solver* s, Plan<R>& P)
 {
     P.d.D = s->D;
@@ -1406,6 +1438,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         fill_plan<double>(s, s->P64);
         fill_plan<float>(s, s->P32);
         fill_tile_map<float>(s, s->P32, s->w32);
+        fill_axis_map<float>(s, s->P32, s->w32);
         // CBS_PLANE=1 / CBS_NO_PLANE=1 force the plane kernels on (where they exist) / off
         s->P32.plane = o.precision != CBS_FP64 && std::getenv("CBS_NO_PLANE") == nullptr &&
                        (std::getenv("CBS_PLANE") != nullptr ? plane_ok<float>(s->P32) : plane_preferred<float>(s->P32));

@@ -67,6 +67,10 @@ template <typename R> struct Plan {
     // is given that field (tile_field) and the error word is set
     CUtensorMap tmap_last;
     const void* tile_field = nullptr;
+    // tensor-copy descriptor of the same field for the pipelined strided-axis kernel (box {COLS, n1, 1})
+    CUtensorMap tmap_axis;
+    const void* axis_field = nullptr;
+    int axis_grid = 0;  // persistent CTAs: SMs x resident blocks
     bool plane = false;    // the Born iteration uses the x-y plane kernels (see plane_ok)
 };
 
@@ -158,11 +162,28 @@ template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x
     return cudaGetLastError();
 }
 
+// pipelined strided-axis kernel: 3D float32, n1 <= 256 (one box per tile)
+template <typename R> __host__ __device__ constexpr bool axis_pipe_ok(int n) { return sizeof(R) == 4 && n >= 16 && n <= 256; }
+
 template <typename R, int N, int S> cudaError_t axis_n(const Plan<R>& P, cplx<R>* w, cudaStream_t st)
 {
     constexpr int RA = r_axis<R>(N);
     constexpr int COLS = cols_axis<R>(N);
     constexpr int T = N / RA;
+    if constexpr (axis_pipe_ok<R>(N)) {
+        if (P.axis_field != nullptr && P.axis_field == (const void*)w && P.err != nullptr && P.axis_grid > 0 &&
+            P.d.n0 % COLS == 0) {
+            using PC = AxisPipeCfg<R, N, COLS>;
+            auto kp = k_axis_fft_pipe<R, N, RA, COLS, S>;
+            static const cudaError_t attr =
+                cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PC::SMEM);
+            if (attr != cudaSuccess) return attr;
+            const long long tiles = (long long)(P.d.D + 1) * P.d.n2 * (P.d.n0 / COLS);
+            const int grid = (int)(tiles < P.axis_grid ? tiles : P.axis_grid);
+            kp<<<grid, T * COLS, PC::SMEM, st>>>(P.tmap_axis, P.d, w, P.tw[1], P.err);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = (size_t)N * COLS * sizeof(cplx<R>);
     auto kern = k_axis_fft<R, N, RA, COLS, S>;
     static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -325,9 +346,35 @@ cudaError_t launch_plane_inv(const Plan<R>& P, cplx<R>* x, const cplx<R>* w, int
     return cudaErrorInvalidValue;
 }
 
+// resident CTAs of the pipelined axis kernel for extent n1 (0 when it does not apply)
+template <typename R> int axis_pipe_blocks_per_sm(int n1)
+{
+    int nb = 0;
+    switch (n1) {
+#define CBS_CASE(n)                                                                                              \
+    case n:                                                                                                      \
+        if constexpr (axis_pipe_ok<R>(n)) {                                                                      \
+            constexpr int RA = r_axis<R>(n), COLS = cols_axis<R>(n);                                             \
+            auto kp = k_axis_fft_pipe<R, n, RA, COLS, -1>;                                                       \
+            if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                                     (int)AxisPipeCfg<R, n, COLS>::SMEM) != cudaSuccess ||                       \
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp, (n / RA) * COLS,                          \
+                                                              AxisPipeCfg<R, n, COLS>::SMEM) != cudaSuccess)     \
+                nb = 0;                                                                                          \
+        }                                                                                                        \
+        break;
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: break;
+    }
+    cudaGetLastError();
+    return nb;
+}
+
 // explicit instantiation helper
 #define CBS_INSTANTIATE_LAUNCHERS(R)                                                                                 \
     template int rows_blocks<R>(const Plan<R>&);                                                                     \
+    template int axis_pipe_blocks_per_sm<R>(int);                                                                    \
     template cudaError_t launch_rows_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int, int,      \
                                             cudaStream_t);                                                           \
     template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R, double*, \
@@ -344,6 +391,7 @@ namespace cbs {
 // declarations for translation units that only call the launchers
 #define CBS_EXTERN_LAUNCHERS(R)                                                                                      \
     extern template int rows_blocks<R>(const Plan<R>&);                                                              \
+    extern template int axis_pipe_blocks_per_sm<R>(int);                                                             \
     extern template cudaError_t launch_rows_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int, int, \
                                                    cudaStream_t);                                                    \
     extern template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R,   \
