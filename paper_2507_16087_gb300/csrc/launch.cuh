@@ -75,9 +75,9 @@ template <typename R> struct Plan {
 };
 
 // x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane.
-// The Born iteration uses them for planes of at most 4096 values: measured on GB300, 64^3 takes 34.1
-// instead of 40.6 us per iteration, while 128 x 128 planes (64 KiB half-planes, two CTAs per SM) take
-// 212 instead of 157 us, so larger planes keep the row + strided-axis kernels.
+// The Born iteration uses them for planes of at most 4096 values: measured on GB300, 64^3 takes 33.0
+// instead of 41.0 us per iteration, while 128 x 128 planes (64 KiB half-planes, two CTAs per SM) take
+// 173 instead of 157 us, so larger planes keep the row + strided-axis kernels.
 constexpr int kPlaneCL = 2;
 constexpr long long kPlaneMaxValues = 4096;
 inline bool plane_size(int n) { return n == 32 || n == 64 || n == 128; }
