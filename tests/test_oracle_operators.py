@@ -83,3 +83,27 @@ def test_green_uniform_symbol_diagonal_in_k():
     g1 = np.roll(P.green(x), (3, 5), axis=(1, 2))
     g2 = P.green(np.roll(x, (3, 5), axis=(1, 2)))
     assert np.max(np.abs(g1 - g2)) <= 1e-13 * np.max(np.abs(g1)) * 10
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (6, 8, 6)])
+def test_collocated_adjoint_operators_are_hermitian_transposes(shape):
+    """App. B's collocated grid: the adjoint (L+I)^-1 and A_s are the Hermitian transposes of the forward ones
+    (dot products), and the adjoint apply equals the conjugate transpose of the densely assembled matrix."""
+    p = _problem(shape, seed=52)
+    P = _oracle(p, collocated=True)
+    a = _rand(P.field_shape, 53)
+    b = _rand(P.field_shape, 54)
+    lhs = np.vdot(b, P.green(a))
+    rhs = np.vdot(P.green(b, adjoint=True), a)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    lhs = np.vdot(b, P.apply(a))
+    rhs = np.vdot(P.apply(b, adjoint=True), a)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    sc = P.scalars()
+    A = dense.assemble(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, p.power, collocated=True)
+    D = len(shape)
+    N = int(np.prod(shape))
+    cinv = np.concatenate([np.full(D * N, sc["lambda1"] ** -0.5), np.full(N, sc["lambda2"] ** -0.5)])
+    As = cinv[:, None] * A * cinv[None, :]
+    ref_h = (np.conj(As).T @ a.ravel()).reshape(a.shape)
+    assert np.linalg.norm(P.apply(a, adjoint=True) - ref_h) <= 1e-13 * np.linalg.norm(ref_h)
