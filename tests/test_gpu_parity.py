@@ -476,3 +476,20 @@ def test_pipelined_axis_kernel_matches_plain_axis_kernel_and_oracle(shape, adjoi
     assert rel(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-6
     xr, _ = P.iterate(y, n_iter=12, nu=0.5, adjoint=adjoint)
     assert rel(x.cpu().numpy(), xr) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(24, 32), (16, 12, 24)])
+def test_collocated_grid_adjoint_matches_oracle(shape):
+    """App. B's collocated variant, adjoint: the conjugate-transposed symbol and the adjoint Born iterations
+    against the oracle."""
+    p, s, _ = make(shape, seed=36, collocated=True)
+    P = O.Problem(p.c0, p.rho, p.alpha, p.dx, p.omega, p.nabs, p.gamma_max, collocated=True)
+    v = W.random_source(shape, 38)
+    out = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.green_apply(T(v), out, adjoint=True)
+    assert rel(out.cpu().numpy(), P.green(v, adjoint=True)) <= 1e-12
+    y = P.scale_source(v, True)
+    x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    s.born_iterate(T(y), x, 30, adjoint=True)
+    xr, _ = P.iterate(y, n_iter=30, nu=0.5, adjoint=True)
+    assert rel(x.cpu().numpy(), xr) <= 1e-11
