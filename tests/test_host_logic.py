@@ -1,0 +1,112 @@
+"""Host-side logic that needs no GPU: the serving request stream and admission rule, the latency
+summary, and the algorithmic byte counts the bench's roofline divides by."""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2507_16087_gb300 import serving as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_request_stream_is_seeded_and_well_formed():
+    a = S.make_requests(n=64, seed=9, rate=5.0, build=False)
+    b = S.make_requests(n=64, seed=9, rate=5.0, build=False)
+    assert [(r.shape, r.ppw, r.seed, r.src_pos, r.arrival) for r in a] == \
+           [(r.shape, r.ppw, r.seed, r.src_pos, r.arrival) for r in b]
+    sizes = {(s, s, s) for s in (64, 96, 128, 192)} | {(s, s) for s in (512, 1024, 2048)}
+    arrivals = [r.arrival for r in a]
+    assert all(t1 > t0 for t0, t1 in zip(arrivals, arrivals[1:]))  # Poisson arrivals are strictly increasing
+    for r in a:
+        assert r.shape in sizes
+        assert 4.0 <= r.ppw <= 8.0
+        assert len(r.src_pos) == len(r.shape)
+        # the source lies inside the absorbing layer's inner edge (n_abs = 16)
+        assert all(16 < q < n - 17 for q, n in zip(r.src_pos, r.shape[::-1]))
+    # mean inter-arrival time close to 1 / rate
+    gaps = np.diff([0.0] + arrivals)
+    assert abs(gaps.mean() - 0.2) < 0.08
+    # all at time zero without a rate
+    assert all(r.arrival == 0.0 for r in S.make_requests(n=8, seed=9, build=False))
+
+
+def test_footprint_grows_with_the_grid_and_covers_the_solver_arrays():
+    f64 = S.footprint_bytes((64, 64, 64))
+    f128 = S.footprint_bytes((128, 128, 128))
+    assert f128 > 7.0 * f64  # 8x the voxels, plus a fixed 16 MiB for tables and partials
+    n = 128 ** 3
+    # x, y, w in float64 and float32 for 4 components, plus the caller's source and result
+    assert f128 >= n * 4 * (3 * 16 + 3 * 8 + 2 * 16)
+    assert S.footprint_bytes((1024, 1024)) > S.footprint_bytes((512, 512))
+
+
+class _FakeServer(S.Server):
+    def __init__(self, free, **kw):
+        super().__init__(**kw)
+        self.free = free
+
+    def _free_bytes(self):
+        return self.free
+
+
+def test_admission_needs_a_slot_and_room_above_the_reserve():
+    srv = _FakeServer(free=20 << 30, max_slots=2, reserve_bytes=8 << 30)
+    assert srv._fits(4 << 30)
+    assert not srv._fits(13 << 30)            # would dip into the reserve
+    srv._reserved = 6 << 30                   # admitted requests that have not allocated yet
+    assert not srv._fits(7 << 30)
+    assert srv._fits(6 << 30)
+    srv._running = 2                          # no free slot
+    assert not srv._fits(1)
+
+
+def test_summary_percentiles_and_throughput():
+    reqs = []
+    for i in range(10):
+        r = S.Request(rid=i, arrival=float(i), shape=(64, 64, 64), ppw=6.0, seed=i, src_pos=(20, 20, 20))
+        r.done = float(i) + 1.0 + 0.1 * i     # latencies 1.0 .. 1.9 s
+        r.iters = 100
+        r.status = "CBS_OK"
+        reqs.append(r)
+    out = S.summarize(reqs)
+    assert out["requests"] == 10
+    assert math.isclose(out["p50_ms"], 1450.0, rel_tol=1e-9)
+    assert math.isclose(out["span_s"], 9.0 + 1.9)
+    assert math.isclose(out["throughput_req_s"], 10 / 10.9)
+    assert out["status"] == {"CBS_OK": 10}
+    assert math.isclose(out["voxel_iters_per_s"], 10 * 64 ** 3 * 100 / 10.9)
+
+
+def test_bench_algorithmic_bytes_per_voxel():
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    b3 = bench.kernel_bytes_per_voxel(3, 4)
+    # float32 3D, C = 4: a complex value is 8 bytes; medium = 3 rs + kp + et = 20 bytes
+    assert b3["rows_fwd"] == 4 * 8 * 3 + 20 == 116
+    assert b3["rows_inv"] == 116
+    assert b3["axis_fwd"] == b3["axis_inv"] == b3["last_symbol"] == 64
+    assert b3["plane_fwd"] == b3["plane_inv"] == 116
+    it = sum(b3[k] for k in ("rows_fwd", "axis_fwd", "last_symbol", "axis_inv", "rows_inv"))
+    assert it == 424
+    b2 = bench.kernel_bytes_per_voxel(2, 4)
+    assert b2["rows_fwd"] == 3 * 8 * 3 + 2 * 4 + 2 * 4  # 2 rs + kp + et
+
+
+@pytest.mark.parametrize("n", [64, 96])
+def test_layered_inversion_workload_is_seeded_and_bounded(n):
+    from paper_2507_16087_gb300 import workloads as W
+
+    d1 = W.layered_inversion(n=n, n_abs=10)
+    d2 = W.layered_inversion(n=n, n_abs=10)
+    assert np.array_equal(d1["c0"], d2["c0"]) and np.array_equal(d1["rho"], d2["rho"])
+    assert d1["c_layered"].min() >= 1400.0 and d1["c_layered"].max() <= 3000.0
+    assert d1["rho_layered"].min() >= 900.0 and d1["rho_layered"].max() <= 2000.0
+    # the perturbation is a few per cent of the layered model
+    rel = np.abs(d1["c0"] / d1["c_layered"] - 1.0)
+    assert rel.max() < 0.2 and rel.std() > 1e-3
