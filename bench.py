@@ -383,7 +383,7 @@ def serving_measure(n_requests, seed=4, n_sat=16, max_slots=6):
     out = S.summarize(reqs)
     out.update({"arrival_rate_req_s": rate, "saturated_req_s": sat["throughput_req_s"],
                 "max_concurrent": srv.max_concurrent, "max_slots": max_slots,
-                "grids": "64^3/96^3/128^3/192^3, 512^2/1024^2/2048^2; FP32+refine to 1e-6"})
+                "grids": "64^3/96^3/128^3/192^3, 512^2/1024^2/2048^2; 250 kHz/500 kHz/1 MHz; FP32+refine to 1e-6"})
     return out
 
 

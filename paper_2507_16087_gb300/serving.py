@@ -47,6 +47,7 @@ class Request:
     ppw: float
     seed: int
     src_pos: tuple                 # (x, y[, z])
+    f_hz: float = W.F0             # source frequency; dx = c_water / (f_hz * ppw)
     problem: W.Problem | None = None
     # filled by the server
     admitted: float = math.nan
@@ -59,11 +60,11 @@ class Request:
 
 
 def make_requests(n=256, seed=4, rate=None, sizes3d=(64, 96, 128, 192), sizes2d=(512, 1024, 2048), n_abs=16,
-                  build=True, device=None):
-    """Seeded request stream: grid uniform over the 3D cubes and 2D squares, medium smoothed noise
-    (sigma = n/16) mapped to c in [1400, 2800], rho in [900, 1900], alpha in [0, 5] dB/cm/MHz, PPW ~ U(4, 8),
-    a point pressure source at a uniform interior voxel; Poisson arrivals at `rate` per second (all at 0
-    when rate is None)."""
+                  build=True, device=None, freqs=(250e3, 500e3, 1e6)):
+    """Seeded request stream: grid uniform over the 3D cubes and 2D squares, frequency uniform over `freqs`,
+    medium smoothed noise (sigma = n/16) mapped to c in [1400, 2800], rho in [900, 1900], alpha in [0, 5]
+    dB/cm/MHz, PPW ~ U(4, 8), a point pressure source at a uniform interior voxel; Poisson arrivals at
+    `rate` per second (all at 0 when rate is None)."""
     rng = np.random.default_rng(seed)
     shapes = [(s, s, s) for s in sizes3d] + [(s, s) for s in sizes2d]
     t = 0.0
@@ -74,7 +75,8 @@ def make_requests(n=256, seed=4, rate=None, sizes3d=(64, 96, 128, 192), sizes2d=
         pos = tuple(int(rng.integers(n_abs + 1, s - n_abs - 1)) for s in shape[::-1])
         if rate:
             t += float(rng.exponential(1.0 / rate))
-        r = Request(rid=i, arrival=t, shape=shape, ppw=ppw, seed=int(rng.integers(0, 2 ** 31)), src_pos=pos)
+        f = float(freqs[int(rng.integers(0, len(freqs)))])
+        r = Request(rid=i, arrival=t, shape=shape, ppw=ppw, seed=int(rng.integers(0, 2 ** 31)), src_pos=pos, f_hz=f)
         if build:
             r.problem = build_problem(r, n_abs, device)
         reqs.append(r)
@@ -85,7 +87,7 @@ def build_problem(r: Request, n_abs=16, device=None) -> W.Problem:
     """The request's medium, generated on the device (torch) by the smooth-random recipe."""
     return W.smooth_random_medium_torch(r.shape, seed=r.seed, c_range=(1400.0, 2800.0), rho_range=(900.0, 1900.0),
                                         alpha_db_range=(0.0, 5.0), sigma_frac=1.0 / 16, ppw=r.ppw, n_abs=n_abs,
-                                        device=device)
+                                        f_hz=r.f_hz, device=device)
 
 
 class Server:

@@ -15,11 +15,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_request_stream_is_seeded_and_well_formed():
     a = S.make_requests(n=64, seed=9, rate=5.0, build=False)
     b = S.make_requests(n=64, seed=9, rate=5.0, build=False)
-    assert [(r.shape, r.ppw, r.seed, r.src_pos, r.arrival) for r in a] == \
-           [(r.shape, r.ppw, r.seed, r.src_pos, r.arrival) for r in b]
+    assert [(r.shape, r.ppw, r.seed, r.src_pos, r.arrival, r.f_hz) for r in a] == \
+           [(r.shape, r.ppw, r.seed, r.src_pos, r.arrival, r.f_hz) for r in b]
     sizes = {(s, s, s) for s in (64, 96, 128, 192)} | {(s, s) for s in (512, 1024, 2048)}
     arrivals = [r.arrival for r in a]
     assert all(t1 > t0 for t0, t1 in zip(arrivals, arrivals[1:]))  # Poisson arrivals are strictly increasing
+    assert {r.f_hz for r in a} == {250e3, 500e3, 1e6}
     for r in a:
         assert r.shape in sizes
         assert 4.0 <= r.ppw <= 8.0
