@@ -167,14 +167,49 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- GPU arm
-# DRAM read + write bytes per launch of each float32 iteration kernel on the 128^3 workload, from one
-# `ncu --set full` capture of the current kernels (null the entry when its kernel changes)
-NCU_TRAFFIC_128 = {"rows_fwd": 180.34e6, "axis_fwd": 67.98e6, "last_symbol": 68.07e6, "axis_inv": 68.11e6,
-                   "rows_inv": 217.05e6}
+def sources_hash() -> str:
+    """Hash of the CUDA sources (csrc/*.cu, *.cuh): a DRAM-traffic figure taken from a profile capture is
+    reported only while the kernels are still the ones that capture measured."""
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_2507_16087_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(path=os.path.join(ROOT, "profiles", "born_iteration_sphere128.md")):
+    """Per-launch DRAM read + write bytes of each iteration kernel from the committed ncu summary, which
+    carries one line `traffic_bytes_per_launch sources=<hash>: kernel=bytes ...`.  Returns (dict, stale):
+    the dict is empty and stale is True when the summary was taken on other kernel sources."""
+    try:
+        with open(path) as f:
+            lines = [ln for ln in f if ln.startswith("traffic_bytes_per_launch")]
+    except OSError:
+        return {}, True
+    if not lines:
+        return {}, True
+    head, _, body = lines[0].partition(":")
+    src = head.split("sources=")[-1].strip()
+    if src != sources_hash():
+        return {}, True
+    out = {}
+    for tok in body.split():
+        k, _, v = tok.partition("=")
+        try:
+            out[k] = float(v)
+        except ValueError:
+            pass
+    return out, False
 
 
 def kernel_bytes_per_voxel(D=3, fp=4):
-    """Algorithmic bytes per voxel of each kernel of one iteration (reads + writes of fields and medium)."""
+    """Bytes per voxel each kernel of one iteration reads and writes as built (fields and the per-voxel
+    medium arrays it streams: rs_eta per velocity component, kp and et for pressure)."""
     C = D + 1
     cb = 2 * fp               # one complex value
     medium = D * fp + 2 * fp  # rs_eta per velocity component + (kp, et) for pressure
@@ -182,6 +217,18 @@ def kernel_bytes_per_voxel(D=3, fp=4):
             "axis_fwd": C * cb * 2, "last_symbol": C * cb * 2, "axis_inv": C * cb * 2,
             "rows_inv": C * cb * 3 + medium,   # w, x in; x out
             "plane_fwd": C * cb * 3 + medium,  # x-y plane kernels: the same reads and writes as the row kernels
+            "plane_inv": C * cb * 3 + medium}
+
+
+def model_bytes_per_voxel(D=3, fp=4):
+    """The byte model of the method's passes: a kernel that reads x, y and the medium (c, rho, alpha in the
+    working precision) and writes w moves C*3 complex values + 3 reals per voxel (108 B in float32 3D);
+    a transform-only pass reads and writes w (64 B)."""
+    C = D + 1
+    cb = 2 * fp
+    medium = 3 * fp
+    return {"rows_fwd": C * cb * 3 + medium, "axis_fwd": C * cb * 2, "last_symbol": C * cb * 2,
+            "axis_inv": C * cb * 2, "rows_inv": C * cb * 3 + medium, "plane_fwd": C * cb * 3 + medium,
             "plane_inv": C * cb * 3 + medium}
 
 
@@ -282,17 +329,27 @@ def run_gpu(args):
     cufft = {"iteration_ms": cufft_ms, "voxel_iters_per_s": Nv / (cufft_ms / 1e3), "own_iteration_ms": own_ms,
              "own_voxel_iters_per_s": Nv / (own_ms / 1e3), "speedup_vs_cufft": cufft_ms / own_ms,
              "what": "same float32 iteration: cuFFT batched C2C plans + plain pointwise kernels (stream launches)"}
-    bpv = kernel_bytes_per_voxel(3, 4)
+    bpv = model_bytes_per_voxel(3, 4)
+    kbpv = kernel_bytes_per_voxel(3, 4)
     peak, peak_kind = _peaks()
     top = max((k for k in kt if bpv.get(k, 0) > 0), key=lambda k: kt[k])
     achieved = bpv[top] * Nv / (kt[top] / 1e3) / 1e9
+    achieved_k = kbpv[top] * Nv / (kt[top] / 1e3) / 1e9
     iter_ms = sum(kt.values())
+    traffic, stale = profile_traffic()
+    per_kernel = {k: {"ms": kt[k], "model_GBs": bpv[k] * Nv / (kt[k] / 1e3) / 1e9,
+                      "frac": bpv[k] * Nv / (kt[k] / 1e3) / 1e9 / peak} for k in kt if bpv.get(k, 0) > 0}
     roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC_128.get(top),
-            "algorithmic_bytes": bpv[top] * Nv,
-            "bytes_per_voxel": bpv[top], "kernel_ms": kt,
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic.get(top),
+            "traffic_source": "profiles/born_iteration_sphere128.md" if not stale else
+                              "null: the committed capture was taken on other kernel sources",
+            "sources": sources_hash(),
+            "algorithmic_bytes": bpv[top] * Nv, "bytes_per_voxel": bpv[top],
+            "kernel_bytes_per_voxel": kbpv[top], "achieved_kernel_bytes": achieved_k,
+            "frac_kernel_bytes": achieved_k / peak, "kernel_ms": kt, "per_kernel": per_kernel,
             "iteration_ms": iter_ms,
-            "iteration_frac": sum(bpv[k] for k in kt) * Nv / (iter_ms / 1e3) / 1e9 / peak}
+            "iteration_frac": sum(bpv[k] for k in kt) * Nv / (iter_ms / 1e3) / 1e9 / peak,
+            "iteration_frac_compulsory": 108 * Nv / (iter_ms / 1e3) / 1e9 / peak}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     hc = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.c0, p.rho, p.alpha)]
@@ -322,9 +379,16 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
+        from oracle import oracle as O
+
         rate, dt, n_cpu, cores = cpu_oracle_rate(p, min_seconds=10.0)
+        O.set_threads(1)
+        rate1, dt1, n1, _ = cpu_oracle_rate(p, min_seconds=5.0)
+        O.set_threads(cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n_cpu} FP64 Born iterations of the same 128^3 workload ({dt:.1f} s)"}
+               "sample": f"{n_cpu} FP64 Born iterations of the same 128^3 workload ({dt:.1f} s)",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{n1} FP64 Born iterations, one thread ({dt1:.1f} s)"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -427,6 +491,53 @@ def run_sweep(args):
     return 0
 
 
+def run_cpu(args):
+    """FP64 CPU oracle voxel-iterations/s at every configuration size, all host cores and one thread:
+    Born iterations of a seeded medium until a few seconds of work (at most 20 iterations); 512^3 all
+    cores only when the host has the memory for it (one iteration takes tens of seconds there, one
+    thread several minutes).  Prints one JSON line."""
+    from oracle import oracle as O
+    from paper_2507_16087_gb300 import workloads as W
+
+    def mem_gb():
+        try:
+            with open("/proc/meminfo") as f:
+                for ln in f:
+                    if ln.startswith("MemAvailable:"):
+                        return int(ln.split()[1]) / 2 ** 20
+        except OSError:
+            pass
+        return 0.0
+
+    cores = O.max_threads()
+    sizes = [(128, 128), (512, 512), (1024, 1024), (2048, 2048), (64,) * 3, (96,) * 3, (128,) * 3, (192,) * 3]
+    if args.n >= 512 and mem_gb() > 80:
+        sizes.append((512,) * 3)
+    rows = []
+    for shape in sizes:
+        nv = int(np.prod(shape))
+        if len(shape) == 3 and shape[0] >= 512:
+            p = W.inclusion_medium(shape, shape[0] // 4, 1800.0, 1300.0, 1.0, n_abs=24)
+        else:
+            p = W.smooth_random_medium(shape, seed=9, n_abs=16)
+        src = np.zeros((len(shape) + 1,) + shape, dtype=np.complex128)
+        src[(len(shape),) + tuple(s // 3 for s in shape)] = 1.0
+        p.source = src
+        row = {"shape": list(shape), "voxels": nv}
+        for threads, key, secs in ((cores, "all_cores", 3.0), (1, "one_thread", 3.0)):
+            if threads == 1 and nv > 2 ** 25:
+                row[key] = None
+                continue
+            O.set_threads(threads)
+            rate, dt, n, used = cpu_oracle_rate(p, min_seconds=secs, max_iter=20)
+            row[key] = {"voxel_iters_per_s": rate, "iters": n, "seconds": dt, "threads": used}
+        O.set_threads(cores)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"mode": "cpu", "cores": cores, "rows": rows}))
+    return 0
+
+
 def run_skull(args):
     """512^3 transcranial-like workload (shell + bowl, 24-cell layer): one FP32 + FP64-refinement solve to
     a 1e-6 residual; prints one JSON line with iterations, time, voxel-iter/s, the float64 residual
@@ -474,10 +585,10 @@ def main():
     ap.add_argument("--nu", type=float, default=0.8)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve", "sweep"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve", "sweep", "cpu"])
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--sat-requests", type=int, default=24)
-    ap.add_argument("--serve-sample", type=int, default=24)
+    ap.add_argument("--serve-sample", type=int, default=256)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -490,6 +601,8 @@ def main():
         return run_serve(args)
     if args.mode == "sweep":
         return run_sweep(args)
+    if args.mode == "cpu":
+        return run_cpu(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

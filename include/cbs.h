@@ -203,19 +203,23 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
 
 /* Allocation-free (L+I)^-1 apply, for callers that cannot call cudaMalloc
  * (code that must stay inside another framework's memory pool or a fixed
- * device-memory budget).  The paper has no counterpart: it is the same float64
- * transform as green_apply, without a solver object.  grid as for
+ * device-memory budget).  The paper has no counterpart: it is the float64
+ * transform green_apply runs for a solver on the staggered grid (App. B.1, the
+ * default grid kind; a collocated-grid solver's green_apply differs), without a
+ * solver object.  grid as for
  * solver_create (extents <= 512, at most 2,097,152 voxels, else CBS_EINVAL with
  * a message from cbs_last_error(NULL)); scalars[0..5] = Re a1, Im a1, Re a2,
  * Im a2, lambda1, lambda2 (as solver_scalars returns them); in, out: distinct
  * caller-owned device complex128 [C][N] buffers; out is also the work array.
- * Work is enqueued on `stream` (cudaStream_t, may be 0) and the call returns
- * once it is complete.  It allocates no device memory: its tables and norm
- * partials live in a static device array of 124 KiB that every GPU loading
- * the library holds until exit.  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress), so make the first call on a
- * device before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * Work is enqueued on `stream` (cudaStream_t, may be 0) and the call
+ * synchronises that stream before it returns.  It allocates no device memory:
+ * its tables and norm partials live in a static device array of 124 KiB that
+ * every GPU loading the library holds until exit.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) and keeps
+ * it for the life of the process, so make the first call on a device before
+ * any stream capture, and do not call it on a device after cudaDeviceReset.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. */
 cbs_status green_apply_noalloc(const cbs_grid* grid, double dx, const double* scalars, const void* in, void* out,
                                int adjoint, void* stream);
 

@@ -967,45 +967,45 @@ cbs_status solve_common(cbs_solver* s, const void* src, void* field, const void*
 }
 
 
-// Minimum enclosing circle (Welzl's randomised incremental algorithm, iterative
-// form, fixed pseudo-random order) of a small host point set: returns the centre.
-double2 mec_centre(std::vector<double2> pts)
+// Minimum enclosing circle of a small host point set (the <= 64 support points),
+// by exhaustion: the smallest enclosing circle passes through two points that
+// are a diameter of it, or through three, so it is the smallest circle among
+// all pair-diameter circles and all three-point circumcircles that contain
+// every point.  O(n^4) for n <= 64 is a few million distance tests.
+double2 mec_centre(const std::vector<double2>& pts)
 {
-    unsigned long long st = 0x9E3779B97F4A7C15ull;
-    for (size_t i = pts.size(); i > 1; --i) {
-        st = st * 6364136223846793005ull + 1442695040888963407ull;
-        std::swap(pts[i - 1], pts[(size_t)((st >> 33) % i)]);
-    }
-    auto dist = [](double2 a, double2 b) { return std::hypot(a.x - b.x, a.y - b.y); };
-    auto circ3 = [](double2 a, double2 b, double2 c, double2& ctr, double& r) {
-        const double d = 2.0 * (a.x * (b.y - c.y) + b.x * (c.y - a.y) + c.x * (a.y - b.y));
-        if (d == 0.0) return false;
-        const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y, c2 = c.x * c.x + c.y * c.y;
-        ctr = make_double2((a2 * (b.y - c.y) + b2 * (c.y - a.y) + c2 * (a.y - b.y)) / d,
-                           (a2 * (c.x - b.x) + b2 * (a.x - c.x) + c2 * (b.x - a.x)) / d);
-        r = std::hypot(a.x - ctr.x, a.y - ctr.y);
+    const size_t n = pts.size();
+    if (n == 0) return make_double2(0.0, 0.0);
+    double best_r = INFINITY;
+    double2 best = pts[0];
+    auto contains_all = [&](double2 ctr, double r) {
+        const double lim = r * (1.0 + 1e-9);
+        for (const double2& p : pts)
+            if (std::hypot(p.x - ctr.x, p.y - ctr.y) > lim) return false;
         return true;
     };
-    const double tol = 1e-12;
-    double2 c = pts[0];
-    double r = 0.0;
-    for (size_t i = 1; i < pts.size(); ++i) {
-        if (dist(pts[i], c) <= r * (1 + tol)) continue;
-        c = pts[i];
-        r = 0.0;
-        for (size_t j = 0; j < i; ++j) {
-            if (dist(pts[j], c) <= r * (1 + tol)) continue;
-            c = make_double2(0.5 * (pts[i].x + pts[j].x), 0.5 * (pts[i].y + pts[j].y));
-            r = 0.5 * dist(pts[i], pts[j]);
-            for (size_t k = 0; k < j; ++k) {
-                if (dist(pts[k], c) <= r * (1 + tol)) continue;
-                double2 cc;
-                double rr;
-                if (circ3(pts[i], pts[j], pts[k], cc, rr)) { c = cc; r = rr; }
+    auto consider = [&](double2 ctr, double r) {
+        if (r < best_r && contains_all(ctr, r)) { best_r = r; best = ctr; }
+    };
+    if (n == 1) return pts[0];
+    for (size_t i = 0; i < n; ++i)
+        for (size_t j = i + 1; j < n; ++j)
+            consider(make_double2(0.5 * (pts[i].x + pts[j].x), 0.5 * (pts[i].y + pts[j].y)),
+                     0.5 * std::hypot(pts[j].x - pts[i].x, pts[j].y - pts[i].y));
+    for (size_t i = 0; i < n; ++i)
+        for (size_t j = i + 1; j < n; ++j)
+            for (size_t k = j + 1; k < n; ++k) {
+                // centre o = p_i + u with 2 (p_j - p_i).u = |p_j - p_i|^2 and 2 (p_k - p_i).u = |p_k - p_i|^2
+                const double bx = pts[j].x - pts[i].x, by = pts[j].y - pts[i].y;
+                const double cx = pts[k].x - pts[i].x, cy = pts[k].y - pts[i].y;
+                const double det = 2.0 * (bx * cy - by * cx);
+                const double scale = (bx * bx + by * by) + (cx * cx + cy * cy);
+                if (!(std::fabs(det) > 1e-14 * scale)) continue;  // (nearly) collinear: a pair circle covers it
+                const double bb = bx * bx + by * by, cc = cx * cx + cy * cy;
+                const double ux = (bb * cy - cc * by) / det, uy = (bx * cc - cx * bb) / det;
+                consider(make_double2(pts[i].x + ux, pts[i].y + uy), std::hypot(ux, uy));
             }
-        }
-    }
-    return c;
+    return best;
 }
 
 // centre of the minimum enclosing circle of the support points of a device value set
@@ -1108,6 +1108,18 @@ template <typename R> void fill_tile_map(cbs_solver* s, Plan<R>& P, const void* 
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r == CUDA_SUCCESS) P.tile_field = field;
     TRACE("tile map for the last axis: %s", r == CUDA_SUCCESS ? "yes" : "no");
+}
+
+// The float32 last-axis step runs on a cluster of C CTAs (one component each) for last-axis extents of at
+// least kLastClusterMin; CBS_LAST_CLUSTER=1 / =0 forces it on (extents 64 .. 2048) / off.
+constexpr int kLastClusterMin = 1 << 30;  // off by default until measured
+bool last_cluster_preferred(const cbs_solver* s)
+{
+    const int nl = s->n[s->D - 1];
+    if (!last_cluster_ok<float>(nl)) return false;
+    const char* e = std::getenv("CBS_LAST_CLUSTER");
+    if (e != nullptr) return e[0] == '1';
+    return nl >= kLastClusterMin;
 }
 
 // Tensor-copy descriptor and persistent grid of the pipelined strided-axis kernel (3D float32, n1 <= 256,
@@ -1442,6 +1454,7 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         // CBS_PLANE=1 / CBS_NO_PLANE=1 force the plane kernels on (where they exist) / off
         s->P32.plane = o.precision != CBS_FP64 && std::getenv("CBS_NO_PLANE") == nullptr &&
                        (std::getenv("CBS_PLANE") != nullptr ? plane_ok<float>(s->P32) : plane_preferred<float>(s->P32));
+        s->P32.last_cluster = o.precision != CBS_FP64 && last_cluster_preferred(s);
         const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)),
                                 std::max(grid_for(n), plane_blocks<float>(s->P32)));
         s->npart = nb;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "born.cuh"
+#include "last_cluster.cuh"
 #include "plane.cuh"
 
 namespace cbs {
@@ -72,6 +73,7 @@ template <typename R> struct Plan {
     const void* axis_field = nullptr;
     int axis_grid = 0;  // persistent CTAs: SMs x resident blocks
     bool plane = false;    // the Born iteration uses the x-y plane kernels (see plane_ok)
+    bool last_cluster = false;  // float32 last-axis step on a cluster of C CTAs (see last_cluster_ok)
 };
 
 // x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane.
@@ -208,8 +210,23 @@ template <typename R, int N, int C> cudaError_t last_tile_n(const Plan<R>& P, cp
     return cudaGetLastError();
 }
 
+// last-axis step on a cluster of C CTAs (one component each): float32, extents 64 .. 2048
+template <typename R> __host__ __device__ constexpr int r_lastcl(int n) { return (n % 3 == 0) ? 12 : 16; }
+template <typename R> __host__ __device__ constexpr int cols_lastcl(int n, int c)
+{
+    return c == 4 ? (n <= 128 ? 32 : (n <= 512 ? 16 : (n <= 1024 ? 8 : 4))) : (n <= 256 ? 16 : 8);
+}
+template <typename R> __host__ __device__ constexpr bool last_cluster_ok(int n)
+{
+    return sizeof(R) == 4 && n >= 64 && n <= 2048;
+}
+template <typename R, int N, int C> cudaError_t last_cluster_n(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st);
+
 template <typename R, int N, int C> cudaError_t last_n(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st)
 {
+    if constexpr (last_cluster_ok<R>(N)) {
+        if (P.last_cluster) return last_cluster_n<R, N, C>(P, w, mode, st);
+    }
     if constexpr (C == 4 && tile_ok<R>(N)) {
         if (P.tile_field != nullptr && P.tile_field == (const void*)w && P.err != nullptr &&
             P.d.n0 % cols_tile<R>(N) == 0)
@@ -279,7 +296,7 @@ template <typename R> cudaError_t launch_last(const Plan<R>& P, cplx<R>* w, int 
     }
 }
 
-template <typename Kern, typename... Args>
+template <int CL = kPlaneCL, typename Kern, typename... Args>
 cudaError_t launch_clustered(Kern kern, int grid, int threads, size_t smem, cudaStream_t st, Args... args)
 {
     cudaLaunchConfig_t cfg{};
@@ -289,12 +306,24 @@ cudaError_t launch_clustered(Kern kern, int grid, int threads, size_t smem, cuda
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kPlaneCL;
+    at[0].val.clusterDim.x = CL;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = kPlaneCL > 1 ? 1 : 0;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename R, int N, int C> cudaError_t last_cluster_n(const Plan<R>& P, cplx<R>* w, int mode, cudaStream_t st)
+{
+    constexpr int RL = r_lastcl<R>(N);
+    constexpr int COLS = cols_lastcl<R>(N, C);
+    using Cfg = LastClusterCfg<R, N, RL, COLS, C>;
+    auto kern = k_last_cluster<R, N, RL, COLS, C>;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    const long long tiles = (long long)(C == 4 ? P.d.n1 : 1) * ((P.d.n0 + COLS - 1) / COLS);
+    return launch_clustered<C>(kern, (int)(C * tiles), Cfg::THREADS, Cfg::SMEM, st, P.d, P.Sy, w, P.tw[P.d.D - 1], mode);
 }
 
 template <typename R, int NX, int NY>

@@ -10,8 +10,10 @@
 // is part of the library image: every GPU that loads the library holds it
 // (kNoAllocScratchDoubles * 8 bytes = 124 KiB) until the process exits.
 //
-// The kernels are the same ones green_apply runs; the output buffer doubles
-// as the transform's work array.
+// The kernels are the same ones green_apply runs for a solver on the
+// staggered grid (App. B.1, the default grid kind); the output buffer doubles
+// as the transform's work array.  The collocated grid kind is not offered
+// here: its symbol uses i k in place of i k e^{i k dx / 2}.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,7 +33,7 @@ using namespace cbs;
 namespace {
 
 constexpr int kMaxAxis = 512;                    // largest supported extent
-constexpr long long kMaxVoxels = 1LL << 21;      // N <= 2,097,152 (e.g. 128^3, 1024 x 2048)
+constexpr long long kMaxVoxels = 1LL << 21;      // N <= 2,097,152 (e.g. 128^3, 512 x 64 x 64, 512 x 512)
 constexpr int kMaxPartialBlocks = 4096;          // inverse-x kernel blocks for N <= kMaxVoxels
 constexpr int kTwOff = 0;                                   // double2 tw[3][kMaxAxis]
 constexpr int kKtOff = kTwOff + 3 * kMaxAxis * 2;           // double2 kt[3][kMaxAxis]
@@ -47,7 +49,10 @@ double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The name
 // g_noalloc_scratch in host code is only a host-side stand-in, so the address
-// is looked up once per device with that device current.
+// is looked up once per device with that device current (the first call on
+// that device) and kept for the life of the process; a process that resets a
+// device with cudaDeviceReset must not call this entry point on that device
+// afterwards, since the kept address belonged to the destroyed context.
 cudaError_t scratch_address(double** out)
 {
     int dev = -1;
