@@ -217,19 +217,21 @@ def kernel_bytes_per_voxel(D=3, fp=4):
             "axis_fwd": C * cb * 2, "last_symbol": C * cb * 2, "axis_inv": C * cb * 2,
             "rows_inv": C * cb * 3 + medium,   # w, x in; x out
             "plane_fwd": C * cb * 3 + medium,  # x-y plane kernels: the same reads and writes as the row kernels
-            "plane_inv": C * cb * 3 + medium}
+            "plane_inv": C * cb * 3 + medium,
+            "rows_inv_fwd": C * cb * 5 + medium}  # w, x, y in; x, w out (update + next forward transform)
 
 
 def model_bytes_per_voxel(D=3, fp=4):
     """The byte model of the method's passes: a kernel that reads x, y and the medium (c, rho, alpha in the
     working precision) and writes w moves C*3 complex values + 3 reals per voxel (108 B in float32 3D);
-    a transform-only pass reads and writes w (64 B)."""
+    a transform-only pass reads and writes w (64 B); the fused update + next forward row pass reads w, x, y
+    and the medium and writes x and w (172 B)."""
     C = D + 1
     cb = 2 * fp
     medium = 3 * fp
     return {"rows_fwd": C * cb * 3 + medium, "axis_fwd": C * cb * 2, "last_symbol": C * cb * 2,
             "axis_inv": C * cb * 2, "rows_inv": C * cb * 3 + medium, "plane_fwd": C * cb * 3 + medium,
-            "plane_inv": C * cb * 3 + medium}
+            "plane_inv": C * cb * 3 + medium, "rows_inv_fwd": C * cb * 5 + medium}
 
 
 def run_gpu(args):
@@ -375,7 +377,7 @@ def run_gpu(args):
 
     serving = None
     if args.serve_sample > 0:
-        serving = serving_measure(args.serve_sample, seed=4, n_sat=min(16, args.serve_sample))
+        serving = serving_measure(args.serve_sample, seed=4, n_sat=min(64, args.serve_sample), max_slots=args.slots)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -429,9 +431,11 @@ def run_kernels(args):
     return 0
 
 
-def serving_measure(n_requests, seed=4, n_sat=16, max_slots=6):
-    """Serving stream: first the saturated throughput from a burst of n_sat requests (all queued at once),
-    then n_requests Poisson arrivals at 0.8 x that rate; returns p50 / p99 latency and throughput."""
+def serving_measure(n_requests, seed=4, n_sat=64, max_slots=6):
+    """Serving stream: the saturated throughput from a burst of n_sat requests of the same mix (all queued at
+    once), then n_requests Poisson arrivals at 0.8 x that rate; p50 / p99 latency over all of them and the
+    aggregate throughput.  Beside it, each grid size solved alone (one request per size, nothing else on the
+    GPU) gives the throughput a one-request-at-a-time server would reach on the same stream."""
     import torch
 
     from paper_2507_16087_gb300 import serving as S
@@ -445,14 +449,28 @@ def serving_measure(n_requests, seed=4, n_sat=16, max_slots=6):
     srv = S.Server(max_slots=max_slots)
     srv.run(reqs, realtime=True)
     out = S.summarize(reqs)
-    out.update({"arrival_rate_req_s": rate, "saturated_req_s": sat["throughput_req_s"],
+    # one request of each grid size alone: seconds per voxel-iteration of that size
+    alone = {}
+    for r in reqs:
+        if r.shape in alone:
+            continue
+        one = S.make_requests(n=1, seed=seed + 2000, device=dev)[0]
+        one.shape, one.src_pos, one.ppw, one.f_hz, one.seed = r.shape, r.src_pos, r.ppw, r.f_hz, r.seed
+        one.problem = S.build_problem(one, device=dev)
+        S.Server(max_slots=1).run([one], realtime=False)
+        alone[r.shape] = (one.done - one.admitted) / max(1, int(np.prod(r.shape)) * one.iters)
+    serial_s = sum(alone[r.shape] * int(np.prod(r.shape)) * r.iters for r in reqs)
+    vox_it = sum(int(np.prod(r.shape)) * r.iters for r in reqs)
+    out.update({"arrival_rate_req_s": rate, "saturated_req_s": sat["throughput_req_s"], "saturation_burst": n_sat,
                 "max_concurrent": srv.max_concurrent, "max_slots": max_slots,
+                "one_at_a_time_voxel_iters_per_s": vox_it / serial_s,
+                "alone_voxel_iters_per_s": {"x".join(map(str, k)): 1.0 / v for k, v in alone.items()},
                 "grids": "64^3/96^3/128^3/192^3, 512^2/1024^2/2048^2; 250 kHz/500 kHz/1 MHz; FP32+refine to 1e-6"})
     return out
 
 
 def run_serve(args):
-    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests)
+    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests, max_slots=args.slots)
     out["mode"] = "serve"
     print(json.dumps(out))
     return 0
@@ -587,7 +605,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve", "sweep", "cpu"])
     ap.add_argument("--requests", type=int, default=256)
-    ap.add_argument("--sat-requests", type=int, default=24)
+    ap.add_argument("--sat-requests", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--serve-sample", type=int, default=256)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=3)

@@ -343,7 +343,20 @@ k_axis_fft(Dims d, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw)
 // ------------------------------------------------------------- last_symbol
 // Forward FFT along the last axis, per-wavenumber symbol on all C components,
 // inverse FFT along the last axis.  grid: (D == 3 ? n1 : 1) * ceil(n0 / COLS).
-template <typename R, int C>
+// 1 / m for the symbol's scale / |mu|^2: float32 takes the approximate reciprocal (2 ulp), float64 the
+// exact quotient
+template <bool FAST, typename R> __device__ __forceinline__ R sym_quot(R a, R m)
+{
+    if constexpr (FAST && sizeof(R) == 4) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"((float)m));
+        return a * r;
+    } else {
+        return a / m;
+    }
+}
+
+template <typename R, int C, bool FAST = false>
 __device__ __forceinline__ void apply_symbol(const Symbol<R>& Sy, int mode, const cplx<R>* t, R k2, cplx<R>* v)
 {
     using CT = cplx<R>;
@@ -357,7 +370,7 @@ __device__ __forceinline__ void apply_symbol(const Symbol<R>& Sy, int mode, cons
         const CT c3 = adj ? cconj(Sy.c3) : Sy.c3;
         // mu = k^2 + (a1 + l1)(a2 + l2);  im = scale / mu
         const CT mu = mk<CT, R>(k2 + c3.x, c3.y);
-        const R inv = Sy.scale / cabs2(mu);
+        const R inv = sym_quot<FAST>(Sy.scale, cabs2(mu));
         const CT im = mk<CT, R>(mu.x * inv, -mu.y * inv);
         CT s = mk<CT, R>((R)0, (R)0);
 #pragma unroll
@@ -388,10 +401,14 @@ __device__ __forceinline__ void apply_symbol(const Symbol<R>& Sy, int mode, cons
 
 // two blocks an SM when a block has fewer than 512 threads; with 512 (the 1024- and 2048-point and 512-point
 // 8-column tiles) the C transforms keep their registers (a 64-register cap spilled them) at one block an SM
-template <typename R, int NL, int RL, int COLS, int C>
+// VAR (measured variants): bit 0 approximate float32 reciprocal in the symbol, bit 1 each twiddle read once
+// for all C transforms
+template <typename R, int NL, int RL, int COLS, int C, int VAR = 0>
 __global__ void __launch_bounds__((NL / RL) * COLS, ((NL / RL) * COLS >= 512) ? 1 : 2)
 k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int mode)
 {
+    constexpr bool FAST = (VAR & 1) != 0;
+    constexpr bool SHTW = (VAR & 2) != 0;
     using CT = cplx<R>;
     constexpr int T = NL / RL;
     constexpr int D = C - 1;
@@ -412,7 +429,7 @@ k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __re
         for (int s = 0; s < RL; ++s)
             v[c][s] = w[(long long)c * d.N + base + (long long)(t + T * slot_q<NL, RL, 0>(s)) * astride];
     const int cstride = NL * COLS;
-    fft_run_multi<NL, RL, C, -1>(v, sm + col, COLS, cstride, t, tw, BlockSync());
+    fft_run_multi<NL, RL, C, -1, 0, SHTW>(v, sm + col, COLS, cstride, t, tw, BlockSync());
     // per-wavenumber symbol
     constexpr int np = plan_npass(NL, RL);
     const int ic0 = valid ? i0 : 0;
@@ -431,7 +448,7 @@ k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __re
         CT vv[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) vv[c] = v[c][s];
-        apply_symbol<R, C>(Sy, mode, tx, k2, vv);
+        apply_symbol<R, C, FAST>(Sy, mode, tx, k2, vv);
 #pragma unroll
         for (int c = 0; c < C; ++c) v[c][s] = vv[c];
     }
@@ -439,7 +456,7 @@ k_last_symbol(Dims d, Symbol<R> Sy, cplx<R>* __restrict__ w, const cplx<R>* __re
     // its registers into the entry order of the inverse transform
 #pragma unroll
     for (int c = 0; c < C; ++c) permute_slots<NL, RL, np, 0>(v[c]);
-    fft_run_multi<NL, RL, C, +1>(v, sm + col, COLS, cstride, t, tw, BlockSync());
+    fft_run_multi<NL, RL, C, +1, 0, SHTW>(v, sm + col, COLS, cstride, t, tw, BlockSync());
     if (valid) {
 #pragma unroll
         for (int c = 0; c < C; ++c)
@@ -552,9 +569,12 @@ k_rows_fwd_bulk(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R
     const long long rest = rest0 + lr;
     const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
     const RowB<R> rb = row_B(M, d.D, c, i1, i2, rest * NX);
-    if (!mbar_wait_bounded(bar, 0)) {
-        if (threadIdx.x == 0) atomicExch(err, kErrBulkTimeout);
-        mbar_wait_bounded(bar, 0);
+    // the decision to leave is block-uniform (no thread may leave while others reach a barrier)
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, kErrBulkTimeout);
+            mbar_wait_bounded(bar, 0);
+        }
         return;
     }
     CT v[RX];
@@ -619,20 +639,24 @@ k_rows_inv_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, cplx<R>* __restric
     const long long rest = rest0 + lr;
     const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
     const RowB<R> rb = row_B(M, d.D, c, i1, i2, rest * NX);
-    bool ok = mbar_wait_bounded(bar, 0);
-    if (!ok) {
-        if (threadIdx.x == 0) atomicExch(err, kErrBulkTimeout);
-        mbar_wait_bounded(bar + 1, 0);
+    // each decision to leave is block-uniform (no thread may leave while others reach a barrier)
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, kErrBulkTimeout);
+            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(bar + 1, 0);
+        }
         return;
     }
     CT v[RX];
 #pragma unroll
     for (int s = 0; s < RX; ++s) v[s] = ws[lr * NX + t + T * slot_q<NX, RX, 0>(s)];
     fft_run<NX, RX, +1, true>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
-    ok = mbar_wait_bounded(bar + 1, 0);
-    if (!ok) {
-        if (threadIdx.x == 0) atomicExch(err, kErrBulkTimeout);
-        mbar_wait_bounded(bar + 1, 0);
+    if (__syncthreads_or(!mbar_wait_bounded(bar + 1, 0))) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, kErrBulkTimeout);
+            mbar_wait_bounded(bar + 1, 0);
+        }
         return;
     }
     R s0 = (R)0, s1 = (R)0;
@@ -651,6 +675,119 @@ k_rows_inv_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, cplx<R>* __restric
         s1 += cabs2(xn);
     }
     block_sum2(s0, s1, partials + 2 * (long long)blockIdx.x);
+}
+
+// ------------------------------------- rows: update of one iteration + start of the next
+// Between two Born iterations the x rows are read and written twice: the
+// inverse row kernel of iteration k updates x (x <- x + nu B (IFFT_x(w) - x))
+// and the forward row kernel of iteration k+1 reads the same x rows again to
+// form FFT_x(B x + y).  Both work row by row, so one kernel does both for a
+// block of rows: w (from the inverse strided-axis pass), x, the medium and y
+// are staged by bulk copies on three barriers (w first, then x and the medium
+// for the update, then y for the next forward transform), B is formed once per
+// value, the updated x is stored and kept in registers, and the next
+// iteration's w = FFT_x(B x + y) is written in place of the consumed w.  Per
+// voxel this moves w, x, y and the medium in and x, w out, instead of also
+// reading x and the medium a second time.  Norm partials as in k_rows_inv_bulk.
+template <typename R, int NX, int RX> struct FusedCfg {
+    using Rc = RowCfg<R, NX, RX>;
+    static constexpr int ROWS = Rc::ROWS;
+    static constexpr int T = Rc::T;
+    static constexpr int THREADS = Rc::THREADS;
+    static constexpr int ELEMS = ROWS * NX;
+    // w (also the exchange), x, y, medium m0, m1, three mbarriers
+    static constexpr size_t SMEM = 3 * (size_t)ELEMS * sizeof(cplx<R>) + 2 * (size_t)ELEMS * sizeof(R) + 32;
+    static constexpr bool OK = (Rc::SL == NX) && ((size_t)ELEMS * sizeof(R)) % 16 == 0;
+};
+
+template <typename R, int NX, int RX>
+__global__ void __launch_bounds__(FusedCfg<R, NX, RX>::THREADS, sizeof(R) == 4 ? 3 : 1)
+k_rows_inv_fwd_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y,
+                    cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int adj, R nu,
+                    double* __restrict__ partials, int* err)
+{
+    using CT = cplx<R>;
+    using Cfg = FusedCfg<R, NX, RX>;
+    constexpr int T = Cfg::T;
+    constexpr int E = Cfg::ELEMS;
+    constexpr int np = plan_npass(NX, RX);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    CT* ws = reinterpret_cast<CT*>(smraw);
+    CT* xs = ws + E;
+    CT* ys = xs + E;
+    R* m0s = reinterpret_cast<R*>(ys + E);
+    R* m1s = m0s + E;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(m1s + E);
+    const int lr = threadIdx.x / T, t = threadIdx.x % T;
+    const long long rows_per_comp = d.N / NX;
+    const long long row0 = (long long)blockIdx.x * Cfg::ROWS;
+    const int c = (int)(row0 / rows_per_comp);
+    const long long rest0 = row0 % rows_per_comp;
+    const long long vbase0 = rest0 * NX;
+    const long long fbase0 = (long long)c * d.N + vbase0;
+    const bool pres = (c == d.D);
+    const R* m0g = (pres ? M.kp : (c == 0 ? M.rs[0] : (c == 1 ? M.rs[1] : M.rs[2]))) + vbase0;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init(bar + 2, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t fb = E * sizeof(CT), mb = E * sizeof(R);
+        mbar_expect_tx(bar, fb);
+        bulk_g2s(ws, w + fbase0, fb, bar);
+        mbar_expect_tx(bar + 1, fb + (pres ? 2 : 1) * mb);
+        bulk_g2s(xs, x + fbase0, fb, bar + 1);
+        bulk_g2s(m0s, m0g, mb, bar + 1);
+        if (pres) bulk_g2s(m1s, M.et + vbase0, mb, bar + 1);
+        mbar_expect_tx(bar + 2, fb);
+        bulk_g2s(ys, y + fbase0, fb, bar + 2);
+    }
+    TwCache<NX, RX, CT> tc;
+    tw_load<NX, RX, T>(tc, t, tw);
+    const long long rest = rest0 + lr;
+    const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
+    const RowB<R> rb = row_B(M, d.D, c, i1, i2, rest * NX);
+    // a timed-out wait records the error, lets the block's remaining copies land and leaves
+    auto fail = [&](int from) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, kErrBulkTimeout);
+            for (int k = from; k < 3; ++k) mbar_wait_bounded(bar + k, 0);
+        }
+    };
+    // every decision to leave is block-uniform (no thread may leave while others reach a barrier)
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) { fail(0); return; }
+    CT v[RX];
+#pragma unroll
+    for (int s = 0; s < RX; ++s) v[s] = ws[lr * NX + t + T * slot_q<NX, RX, 0>(s)];
+    fft_run<NX, RX, +1, true>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
+    if (__syncthreads_or(!mbar_wait_bounded(bar + 1, 0))) { fail(1); return; }
+    R s0 = (R)0, s1 = (R)0;
+    const long long fbase = fbase0 + (long long)lr * NX;
+#pragma unroll
+    for (int s = 0; s < RX; ++s) {
+        const int i0 = t + T * slot_q<NX, RX, np>(s);
+        const int e = lr * NX + i0;
+        const R g = __ldg(rb.g0 + i0) + rb.grest;
+        const CT b = born_B_vals(M, pres, g, m0s[e], pres ? m1s[e] : (R)0, adj != 0);
+        const CT xv = xs[e];
+        const CT del = cscale(cmul(b, csub(v[s], xv)), nu);
+        const CT xn = cadd(xv, del);
+        x[fbase + i0] = xn;
+        s0 += cabs2(del);
+        s1 += cabs2(xn);
+        v[s] = cmul(b, xn);  // B x of the next iteration
+    }
+    block_sum2(s0, s1, partials + 2 * (long long)blockIdx.x);
+    if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0))) { fail(2); return; }
+#pragma unroll
+    for (int s = 0; s < RX; ++s) v[s] = cadd(v[s], ys[lr * NX + t + T * slot_q<NX, RX, np>(s)]);
+    // same positions, entry order of the forward transform
+    permute_slots<NX, RX, np, 0>(v);
+    fft_run<NX, RX, -1, true>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
+#pragma unroll
+    for (int s = 0; s < RX; ++s) w[fbase + t + T * slot_q<NX, RX, np>(s)] = v[s];
 }
 
 // ------------------------------------------ tensor-copy helpers (3D tiles)

@@ -610,11 +610,34 @@ template <typename R> void iterate_once(cbs_solver* s, bool adj, int slot)
     s->launches += (s->D == 3) ? 5 : 3;
 }
 
-// n <= kslots iterations and one reduction of their norms into hist[0..n)
+// n <= kslots iterations and one reduction of their norms into hist[0..n).  With fused rows the update of
+// iteration k and the forward row transform of iteration k+1 are one kernel: the block launches the forward
+// row kernel once, then per iteration the strided-axis / last-axis kernels and the fused row kernel, the last
+// iteration ending with the plain update kernel.
 template <typename R> void iterate_block(cbs_solver* s, int n, bool adj)
 {
-    for (int k = 0; k < n; ++k) iterate_once<R>(s, adj, k);
-    reduce_slots(s, iter_blocks<R>(Bufs<R>::plan(s)), n, s->hist);
+    Plan<R>& P = Bufs<R>::plan(s);
+    if (P.plane || !P.fused_rows) {
+        for (int k = 0; k < n; ++k) iterate_once<R>(s, adj, k);
+    } else {
+        auto x = Bufs<R>::x(s);
+        auto y = Bufs<R>::y(s);
+        auto w = Bufs<R>::w(s);
+        const int nblk = rows_blocks<R>(P);
+        const R nu = (R)s->opt.nu;
+        CUDA_TRY(launch_rows_fwd<R>(P, x, y, w, FWD_BORN, adj, s->st));
+        s->launches += 1;
+        for (int k = 0; k < n; ++k) {
+            if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, -1, s->st));
+            CUDA_TRY(launch_last<R>(P, w, adj ? SYM_GREEN_ADJ : SYM_GREEN, s->st));
+            if (s->D == 3) CUDA_TRY(launch_axis<R>(P, w, +1, s->st));
+            double* part = s->partials + (size_t)k * nblk * 2;
+            if (k + 1 < n) CUDA_TRY(launch_rows_inv_fwd<R>(P, x, y, w, adj, nu, part, s->st));
+            else CUDA_TRY(launch_rows_inv<R>(P, x, y, w, INV_BORN, adj, nu, part, s->st));
+            s->launches += (s->D == 3) ? 4 : 2;
+        }
+    }
+    reduce_slots(s, iter_blocks<R>(P), n, s->hist);
 }
 
 // run n iterations in blocks of K = kslots; full blocks replay a captured CUDA graph
@@ -1110,16 +1133,18 @@ template <typename R> void fill_tile_map(cbs_solver* s, Plan<R>& P, const void* 
     TRACE("tile map for the last axis: %s", r == CUDA_SUCCESS ? "yes" : "no");
 }
 
-// The float32 last-axis step runs on a cluster of C CTAs (one component each) for last-axis extents of at
-// least kLastClusterMin; CBS_LAST_CLUSTER=1 / =0 forces it on (extents 64 .. 2048) / off.
-constexpr int kLastClusterMin = 1 << 30;  // off by default until measured
+// The float32 last-axis step runs on a cluster of C CTAs (one component each) for 2D grids whose last axis
+// has 2048 points: measured on GB300, 2048^2 takes 142.5 instead of 170.7 us (8-column tiles, 64-byte rows,
+// instead of 2-column tiles holding all three components).  Elsewhere the one-CTA kernel is faster (128^3:
+// 37.9 against 53.5 us; 512^3: 3.25 against 4.26 ms; 1024^2: 32.9 against 34.9 us).  CBS_LAST_CLUSTER=1 /
+// =0 forces it on (extents 64 .. 2048) / off.
 bool last_cluster_preferred(const cbs_solver* s)
 {
     const int nl = s->n[s->D - 1];
     if (!last_cluster_ok<float>(nl)) return false;
     const char* e = std::getenv("CBS_LAST_CLUSTER");
     if (e != nullptr) return e[0] == '1';
-    return nl >= kLastClusterMin;
+    return s->D == 2 && nl >= 2048;
 }
 
 // Tensor-copy descriptor and persistent grid of the pipelined strided-axis kernel (3D float32, n1 <= 256,
@@ -1455,6 +1480,11 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         s->P32.plane = o.precision != CBS_FP64 && std::getenv("CBS_NO_PLANE") == nullptr &&
                        (std::getenv("CBS_PLANE") != nullptr ? plane_ok<float>(s->P32) : plane_preferred<float>(s->P32));
         s->P32.last_cluster = o.precision != CBS_FP64 && last_cluster_preferred(s);
+        // CBS_PLANE_CL=4: four CTAs per x-y plane (quarter planes) in place of a pair
+        {
+            const char* e = std::getenv("CBS_PLANE_CL");
+            s->P32.plane_cl = (e != nullptr && e[0] == '4') ? 4 : 2;
+        }
         const int nb = std::max(std::max(rows_blocks<double>(s->P64), rows_blocks<float>(s->P32)),
                                 std::max(grid_for(n), plane_blocks<float>(s->P32)));
         s->npart = nb;
@@ -1467,6 +1497,13 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         CUDA_TRY(cudaMemsetAsync(s->errword, 0, sizeof(int), s->st));
         s->P64.err = s->errword;
         s->P32.err = s->errword;
+        // one kernel for the update of an iteration and the forward row transform of the next, where the rows
+        // are bulk-staged; CBS_NO_FUSED_ROWS=1 keeps them apart
+        {
+            const bool off = std::getenv("CBS_NO_FUSED_ROWS") != nullptr;
+            s->P64.fused_rows = !off && fused_rows_ok<double>(s->P64);
+            s->P32.fused_rows = !off && o.precision != CBS_FP64 && fused_rows_ok<float>(s->P32);
+        }
         CUDA_TRY(cudaEventRecord(s->ev1, s->st));
         CUDA_TRY(cudaStreamSynchronize(s->st));
         float ms = 0;
@@ -1669,9 +1706,12 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
     const char* kn3[5] = {"rows_fwd", "axis_fwd", "last_symbol", "axis_inv", "rows_inv"};
     const char* kn2[3] = {"rows_fwd", "last_symbol", "rows_inv"};
     const char* knp[3] = {"plane_fwd", "last_symbol", "plane_inv"};
+    const char* knf3[4] = {"axis_fwd", "last_symbol", "axis_inv", "rows_inv_fwd"};
+    const char* knf2[2] = {"last_symbol", "rows_inv_fwd"};
     const bool plane = f32 && s->P32.plane;
-    const int K = (s->D == 3 && !plane) ? 5 : 3;
-    const char** kn = plane ? knp : (s->D == 3 ? kn3 : kn2);
+    const bool fused = !plane && (f32 ? s->P32.fused_rows : s->P64.fused_rows);
+    const int K = fused ? (s->D == 3 ? 4 : 2) : ((s->D == 3 && !plane) ? 5 : 3);
+    const char** kn = fused ? (s->D == 3 ? knf3 : knf2) : (plane ? knp : (s->D == 3 ? kn3 : kn2));
     try {
         begin_call(s);
         const long long n = field_len(s);
@@ -1685,10 +1725,33 @@ cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter
         std::vector<cudaEvent_t> ev(K + 1);
         for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
         std::vector<double> acc(K, 0.0);
+        // fused rows: the forward row kernel runs once before the timed iterations, each of which is then the
+        // strided-axis and last-axis kernels and the fused update + next forward row kernel
+        if (fused) {
+            if (f32) CUDA_TRY(launch_rows_fwd<float>(s->P32, s->x32, s->y32, s->w32, FWD_BORN, 0, s->st));
+            else CUDA_TRY(launch_rows_fwd<double>(s->P64, s->x64, s->y64, s->w64, FWD_BORN, 0, s->st));
+        }
         for (int it = 0; it < n_iter; ++it) {
             int k = 0;
             auto mark = [&]() { CUDA_TRY(cudaEventRecord(ev[k++], s->st)); };
             mark();
+            if (fused) {
+                auto one = [&](auto& P, auto* x, auto* y, auto* w, auto nu) {
+                    if (s->D == 3) { CUDA_TRY(launch_axis(P, w, -1, s->st)); mark(); }
+                    CUDA_TRY(launch_last(P, w, SYM_GREEN, s->st)); mark();
+                    if (s->D == 3) { CUDA_TRY(launch_axis(P, w, +1, s->st)); mark(); }
+                    CUDA_TRY(launch_rows_inv_fwd(P, x, y, w, 0, nu, s->partials, s->st)); mark();
+                };
+                if (f32) one(s->P32, s->x32, s->y32, s->w32, (float)s->opt.nu);
+                else one(s->P64, s->x64, s->y64, s->w64, s->opt.nu);
+                CUDA_TRY(cudaStreamSynchronize(s->st));
+                for (int j = 0; j < K; ++j) {
+                    float tj = 0;
+                    CUDA_TRY(cudaEventElapsedTime(&tj, ev[j], ev[j + 1]));
+                    acc[j] += tj;
+                }
+                continue;
+            }
             if (f32) {
                 Plan<float>& P = s->P32;
                 if (plane) {

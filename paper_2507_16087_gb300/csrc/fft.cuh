@@ -343,11 +343,35 @@ __device__ __forceinline__ void fft_run(CT (&v)[R], CT* sm, int ss, int tid, con
     }
 }
 
+// One pass of C transforms that share the thread mapping: each twiddle is read
+// from the table once and applied to all C components.
+template <int N, int R, int T, int P, int S, int C, typename CT>
+__device__ __forceinline__ void pass_compute_multi(CT (&v)[C][R], int tid, const CT* __restrict__ tw)
+{
+    constexpr int r = plan_radix(N, R, P);
+    constexpr int NS = plan_ns(N, R, P);
+#pragma unroll
+    for (int m = 0; m < R / r; ++m) {
+        if constexpr (NS > 1) {
+            const int jj = (tid + T * m) % NS;
+#pragma unroll
+            for (int k = 1; k < r; ++k) {
+                const CT w = __ldg(&tw[jj * k * (N / (NS * r))]);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    v[c][m * r + k] = (S < 0) ? cmul(v[c][m * r + k], w) : cmulc(v[c][m * r + k], w);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) dft<r, S>(&v[c][m * r]);
+    }
+}
+
 // Same for C independent transforms that share the thread mapping (used to
 // keep all components of a pencil in registers at once).
 // (twiddles read from the table: with C transforms in registers there is no
-// room to cache them)
-template <int N, int R, int C, int S, int P = 0, typename CT, typename Sync>
+// room to cache them; SHTW reads each one once for all C transforms)
+template <int N, int R, int C, int S, int P = 0, bool SHTW = false, typename CT, typename Sync>
 __device__ __forceinline__ void fft_run_multi(CT (&v)[C][R], CT* sm, int ss, int cstride, int tid,
                                               const CT* __restrict__ tw, Sync sync)
 {
@@ -355,8 +379,12 @@ __device__ __forceinline__ void fft_run_multi(CT (&v)[C][R], CT* sm, int ss, int
     constexpr int np = plan_npass(N, R);
     static_assert(np > 0, "unsupported FFT size / register split");
     const TwCache<N, R, CT> none{};
+    if constexpr (SHTW) {
+        pass_compute_multi<N, R, T, P, S, C>(v, tid, tw);
+    } else {
 #pragma unroll
-    for (int c = 0; c < C; ++c) pass_compute<N, R, T, P, S, false>(v[c], tid, tw, none);
+        for (int c = 0; c < C; ++c) pass_compute<N, R, T, P, S, false>(v[c], tid, tw, none);
+    }
     if constexpr (P + 1 < np) {
         constexpr int r = plan_radix(N, R, P);
         constexpr int NS = plan_ns(N, R, P);
@@ -380,7 +408,7 @@ __device__ __forceinline__ void fft_run_multi(CT (&v)[C][R], CT* sm, int ss, int
 #pragma unroll
                 for (int k = 0; k < rn; ++k) v[c][m * rn + k] = sm[c * cstride + (j + k * (N / rn)) * ss];
             }
-        fft_run_multi<N, R, C, S, P + 1>(v, sm, ss, cstride, tid, tw, sync);
+        fft_run_multi<N, R, C, S, P + 1, SHTW>(v, sm, ss, cstride, tid, tw, sync);
     }
 }
 

@@ -74,6 +74,8 @@ template <typename R> struct Plan {
     int axis_grid = 0;  // persistent CTAs: SMs x resident blocks
     bool plane = false;    // the Born iteration uses the x-y plane kernels (see plane_ok)
     bool last_cluster = false;  // float32 last-axis step on a cluster of C CTAs (see last_cluster_ok)
+    int plane_cl = 2;           // CTAs per x-y plane of the plane kernels (2 or 4)
+    bool fused_rows = false;    // update + next forward row transform in one kernel (see fused_rows_ok)
 };
 
 // x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane.
@@ -91,7 +93,7 @@ template <typename R> inline bool plane_preferred(const Plan<R>& P)
 {
     return plane_ok<R>(P) && (long long)P.d.n0 * P.d.n1 <= kPlaneMaxValues;
 }
-template <typename R> inline int plane_blocks(const Plan<R>& P) { return (P.d.D + 1) * P.d.n2 * kPlaneCL; }
+template <typename R> inline int plane_blocks(const Plan<R>& P) { return (P.d.D + 1) * P.d.n2 * P.plane_cl; }
 
 // the Born row kernels stage their rows with bulk copies when every block's
 // rows lie in one component and the rows' exchange fits in place
@@ -162,6 +164,53 @@ template <typename R, int N> cudaError_t rows_inv_n(const Plan<R>& P, cplx<R>* x
     else
         k_rows_inv<R, N, RX, false><<<grid, Cfg::THREADS, 0, st>>>(P.d, P.M, x, y, w, P.tw[0], mode, adj, nu, partials);
     return cudaGetLastError();
+}
+
+// update of iteration k fused with the forward row transform of iteration k+1 (bulk-staged rows)
+template <typename R, int N> inline bool fused_rows_ok_n(const Plan<R>& P)
+{
+    using Cfg = FusedCfg<R, N, r_rows<R>(N)>;
+    return Cfg::OK && P.err != nullptr && (P.d.N / N) % Cfg::ROWS == 0;
+}
+
+template <typename R> inline bool fused_rows_ok(const Plan<R>& P)
+{
+    switch (P.d.n0) {
+#define CBS_CASE(n) case n: return fused_rows_ok_n<R, n>(P);
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return false;
+    }
+}
+
+template <typename R, int N> cudaError_t rows_inv_fwd_n(const Plan<R>& P, cplx<R>* x, const cplx<R>* y, cplx<R>* w,
+                                                        int adj, R nu, double* partials, cudaStream_t st)
+{
+    constexpr int RX = r_rows<R>(N);
+    using Cfg = FusedCfg<R, N, RX>;
+    if constexpr (Cfg::OK) {
+        if (!fused_rows_ok_n<R, N>(P)) return cudaErrorNotSupported;
+        auto kern = k_rows_inv_fwd_bulk<R, N, RX>;
+        static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (attr != cudaSuccess) return attr;
+        const long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
+        kern<<<(unsigned)(rows / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, st>>>(P.d, P.M, x, y, w, P.tw[0], adj, nu, partials,
+                                                                            P.err);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+template <typename R> cudaError_t launch_rows_inv_fwd(const Plan<R>& P, cplx<R>* x, const cplx<R>* y, cplx<R>* w, int adj,
+                                                      R nu, double* partials, cudaStream_t st)
+{
+    switch (P.d.n0) {
+#define CBS_CASE(n) case n: return rows_inv_fwd_n<R, n>(P, x, y, w, adj, nu, partials, st);
+        CBS_FOR_EACH_SIZE(CBS_CASE)
+#undef CBS_CASE
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // pipelined strided-axis kernel: 3D float32, n1 <= 256 (one box per tile)
@@ -326,26 +375,40 @@ template <typename R, int N, int C> cudaError_t last_cluster_n(const Plan<R>& P,
     return launch_clustered<C>(kern, (int)(C * tiles), Cfg::THREADS, Cfg::SMEM, st, P.d, P.Sy, w, P.tw[P.d.D - 1], mode);
 }
 
+template <typename R, int NX, int NY, int CL>
+cudaError_t plane_fwd_cl(const Plan<R>& P, const cplx<R>* x, const cplx<R>* y, cplx<R>* w, int adj, cudaStream_t st)
+{
+    using Cfg = PlaneCfg<R, NX, NY, CL>;
+    auto kern = k_plane_fwd<R, NX, NY, CL>;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    return launch_clustered<CL>(kern, plane_blocks<R>(P), Cfg::THREADS, Cfg::SMEM, st, P.d, P.M, x, y, w, P.tw[0],
+                                P.tw[1], adj);
+}
+
+template <typename R, int NX, int NY, int CL>
+cudaError_t plane_inv_cl(const Plan<R>& P, cplx<R>* x, const cplx<R>* w, int adj, R nu, double* partials, cudaStream_t st)
+{
+    using Cfg = PlaneCfg<R, NX, NY, CL>;
+    auto kern = k_plane_inv<R, NX, NY, CL>;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    return launch_clustered<CL>(kern, plane_blocks<R>(P), Cfg::THREADS, Cfg::SMEM, st, P.d, P.M, x, w, P.tw[0], P.tw[1],
+                                adj, nu, partials);
+}
+
 template <typename R, int NX, int NY>
 cudaError_t plane_fwd_n(const Plan<R>& P, const cplx<R>* x, const cplx<R>* y, cplx<R>* w, int adj, cudaStream_t st)
 {
-    using Cfg = PlaneCfg<R, NX, NY, kPlaneCL>;
-    auto kern = k_plane_fwd<R, NX, NY, kPlaneCL>;
-    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-    if (attr != cudaSuccess) return attr;
-    return launch_clustered(kern, plane_blocks<R>(P), Cfg::THREADS, Cfg::SMEM, st, P.d, P.M, x, y, w, P.tw[0],
-                            P.tw[1], adj);
+    if (P.plane_cl == 4) return plane_fwd_cl<R, NX, NY, 4>(P, x, y, w, adj, st);
+    return plane_fwd_cl<R, NX, NY, 2>(P, x, y, w, adj, st);
 }
 
 template <typename R, int NX, int NY>
 cudaError_t plane_inv_n(const Plan<R>& P, cplx<R>* x, const cplx<R>* w, int adj, R nu, double* partials, cudaStream_t st)
 {
-    using Cfg = PlaneCfg<R, NX, NY, kPlaneCL>;
-    auto kern = k_plane_inv<R, NX, NY, kPlaneCL>;
-    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-    if (attr != cudaSuccess) return attr;
-    return launch_clustered(kern, plane_blocks<R>(P), Cfg::THREADS, Cfg::SMEM, st, P.d, P.M, x, w, P.tw[0], P.tw[1],
-                            adj, nu, partials);
+    if (P.plane_cl == 4) return plane_inv_cl<R, NX, NY, 4>(P, x, w, adj, nu, partials, st);
+    return plane_inv_cl<R, NX, NY, 2>(P, x, w, adj, nu, partials, st);
 }
 
 #define CBS_FOR_EACH_PLANE(X) X(32, 32) X(32, 64) X(32, 128) X(64, 32) X(64, 64) X(64, 128) X(128, 32) X(128, 64) X(128, 128)
@@ -408,6 +471,9 @@ template <typename R> int axis_pipe_blocks_per_sm(int n1)
                                             cudaStream_t);                                                           \
     template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R, double*, \
                                             cudaStream_t);                                                           \
+    template cudaError_t launch_rows_inv_fwd<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, R, double*,  \
+                                                cudaStream_t);                                                       \
+    template bool fused_rows_ok<R>(const Plan<R>&);                                                                  \
     template cudaError_t launch_axis<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                                \
     template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                                \
     template cudaError_t launch_plane_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int,          \
@@ -425,6 +491,9 @@ namespace cbs {
                                                    cudaStream_t);                                                    \
     extern template cudaError_t launch_rows_inv<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, int, R,   \
                                                    double*, cudaStream_t);                                           \
+    extern template cudaError_t launch_rows_inv_fwd<R>(const Plan<R>&, cplx<R>*, const cplx<R>*, cplx<R>*, int, R,    \
+                                                       double*, cudaStream_t);                                       \
+    extern template bool fused_rows_ok<R>(const Plan<R>&);                                                           \
     extern template cudaError_t launch_axis<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                         \
     extern template cudaError_t launch_last<R>(const Plan<R>&, cplx<R>*, int, cudaStream_t);                         \
     extern template cudaError_t launch_plane_fwd<R>(const Plan<R>&, const cplx<R>*, const cplx<R>*, cplx<R>*, int,   \

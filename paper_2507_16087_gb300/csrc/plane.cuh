@@ -27,7 +27,8 @@ template <typename R, int NX, int NY, int CL> struct PlaneCfg {
     static constexpr int ROWS_OWN = NY / CL;    // plane rows held by one CTA
     static constexpr int COLS_OWN = NX / CL;    // columns one CTA transforms along y
     static constexpr int T0 = TX * ROWS_OWN < TY * COLS_OWN ? TX * ROWS_OWN : TY * COLS_OWN;
-    static constexpr int THREADS = T0 < 512 ? T0 : 512;
+    static constexpr int TMAX = CL >= 4 ? 256 : 512;  // quarter planes: smaller CTAs, more of them an SM
+    static constexpr int THREADS = T0 < TMAX ? T0 : TMAX;
     static constexpr int RB = THREADS / TX;     // rows per x batch
     static constexpr int CB = THREADS / TY;     // columns per y batch
     static constexpr int SL = sm_len<NX, true>();
@@ -38,7 +39,7 @@ template <typename R, int NX, int NY, int CL> struct PlaneCfg {
     static_assert(THREADS % 32 == 0 && THREADS % TX == 0 && THREADS % TY == 0, "plane block shape");
     static_assert(ROWS_OWN % RB == 0 && COLS_OWN % CB == 0, "plane batches");
     static_assert(TX <= 32, "a row's threads must lie in one warp");
-    static_assert(CL == 1 || CL == 2, "one CTA or a pair per plane");
+    static_assert(CL == 1 || CL == 2 || CL == 4, "one CTA, a pair or four per plane");
 };
 
 template <int CL> __device__ __forceinline__ unsigned plane_rank()
@@ -53,11 +54,18 @@ template <int CL> __device__ __forceinline__ void plane_sync()
     else cooperative_groups::this_cluster().sync();
 }
 
-// shared-memory base of the half-plane held by CTA `q` of the cluster (CL <= 2)
+// shared-memory base of the part of the plane held by CTA `q` of the cluster
 template <int CL, typename CT> __device__ __forceinline__ CT* plane_half(CT* H, unsigned q)
 {
     if constexpr (CL == 1) return H;
     else return cooperative_groups::this_cluster().map_shared_rank(H, q);
+}
+
+// the plane row i1 (of NY) as held in the cluster: CTA i1 / ROWS_OWN, local row i1 % ROWS_OWN
+template <int CL, int ROWS_OWN, int SL, typename CT> __device__ __forceinline__ CT* plane_row(CT* H, int i1)
+{
+    if constexpr (CL == 1) return H + i1 * SL;
+    else return plane_half<CL>(H, (unsigned)(i1 / ROWS_OWN)) + (i1 % ROWS_OWN) * SL;
 }
 
 // w[c, z] = FFT_y FFT_x (B x + y) of plane (c, z) = blockIdx.x / CL.
@@ -112,8 +120,6 @@ k_plane_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* _
         TwCache<NY, RY, CT> tc;
         tw_load<NY, RY, TY>(tc, t, twy);
         constexpr int np = plan_npass(NY, RY);
-        CT* const h0 = plane_half<CL>(H, 0u);
-        CT* const h1 = plane_half<CL>(H, (unsigned)(CL - 1));
 #pragma unroll 1
         for (int b = 0; b < Cfg::COLS_OWN / Cfg::CB; ++b) {
             const int i0 = (int)rank * Cfg::COLS_OWN + b * Cfg::CB + col;
@@ -122,7 +128,7 @@ k_plane_fwd(Dims d, Medium<R> M, const cplx<R>* __restrict__ x, const cplx<R>* _
 #pragma unroll
             for (int s = 0; s < RY; ++s) {
                 const int i1 = t + TY * slot_q<NY, RY, 0>(s);
-                v[s] = (i1 < Cfg::ROWS_OWN ? h0 : h1)[(i1 % Cfg::ROWS_OWN) * SL + sw];
+                v[s] = plane_row<CL, Cfg::ROWS_OWN, SL>(H, i1)[sw];
             }
             fft_run<NY, RY, -1>(v, X + col, Cfg::CB, t, twy, tc, BlockSync());
 #pragma unroll
@@ -158,8 +164,6 @@ k_plane_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restr
         TwCache<NY, RY, CT> tc;
         tw_load<NY, RY, TY>(tc, t, twy);
         constexpr int np = plan_npass(NY, RY);
-        CT* const h0 = plane_half<CL>(H, 0u);
-        CT* const h1 = plane_half<CL>(H, (unsigned)(CL - 1));
 #pragma unroll 1
         for (int b = 0; b < Cfg::COLS_OWN / Cfg::CB; ++b) {
             const int i0 = (int)rank * Cfg::COLS_OWN + b * Cfg::CB + col;
@@ -171,7 +175,7 @@ k_plane_inv(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restr
 #pragma unroll
             for (int s = 0; s < RY; ++s) {
                 const int i1 = t + TY * slot_q<NY, RY, np>(s);
-                (i1 < Cfg::ROWS_OWN ? h0 : h1)[(i1 % Cfg::ROWS_OWN) * SL + sw] = v[s];
+                plane_row<CL, Cfg::ROWS_OWN, SL>(H, i1)[sw] = v[s];
             }
         }
     }

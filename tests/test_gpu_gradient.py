@@ -134,7 +134,7 @@ def _fd_check(n, n_abs, n_vox, tol_solve, rel_tol):
 
 
 def test_gradient_central_differences_64():
-    _fd_check(64, 10, 10, 1e-11, 1e-3)
+    _fd_check(64, 10, 10, 1e-12, 1e-3)
 
 
 def test_gradient_central_differences_128_and_checkpointing():
@@ -142,34 +142,12 @@ def test_gradient_central_differences_128_and_checkpointing():
     at 20 voxels within 1e-3; the checkpointed backward gives the stored-field gradient."""
     from paper_2507_16087_gb300 import autograd as AG
 
-    worst, gc, gr, d, data, rec = _fd_check(128, 20, 20, 1e-11, 1e-3)
+    worst, gc, gr, d, data, rec = _fd_check(128, 20, 20, 1e-12, 1e-3)
     # the recomputing (checkpointed) backward gives the same gradient
     c0 = T(d["c0"]).requires_grad_(True)
     rho = T(d["rho"]).requires_grad_(True)
     f = AG.helmholtz_fields(c0, rho, T(d["alpha"]), T(d["sources"]), d["dx"], d["omega"], d["nabs"], d["gamma_max"],
-                            precision="fp32_refine", tol=1e-11, checkpoint=True)
+                            precision="fp32_refine", tol=1e-12, checkpoint=True)
     AG.receiver_misfit(f, data, rec).backward()
     assert np.linalg.norm(c0.grad.cpu().numpy() - gc) <= 1e-9 * np.linalg.norm(gc)
     assert np.linalg.norm(rho.grad.cpu().numpy() - gr) <= 1e-9 * np.linalg.norm(gr)
-
-
-@pytest.mark.oracle_job("gradient64")
-def test_autograd_gradient_matches_oracle_64(oracle_job):
-    """The layered-inversion medium at 64^3 (two sources, 64 receivers, seeded receiver data): misfit and
-    gradient through torch.autograd (FP32 + refinement solves to 1e-10) against the oracle's forward and
-    adjoint solves and gradient formula (run in the background)."""
-    import oracle_jobs as OJ
-    from paper_2507_16087_gb300 import autograd as AG
-
-    d = OJ.gradient64_inputs()
-    c0 = T(d["c0"]).requires_grad_(True)
-    rho = T(d["rho"]).requires_grad_(True)
-    f = AG.helmholtz_fields(c0, rho, T(d["alpha"]), T(d["sources"]), d["dx"], d["omega"], d["nabs"],
-                            d["gamma_max"], precision="fp32_refine", tol=OJ.GRAD64["tol"])
-    rec = tuple(torch.tensor(r, device=DEV) for r in d["receivers"])
-    J = AG.receiver_misfit(f, T(d["data"]), rec)
-    J.backward()
-    Jo = float(oracle_job["J"])
-    assert abs(J.item() - Jo) <= 1e-7 * Jo
-    for got, ref in ((c0.grad, oracle_job["grad_c0"]), (rho.grad, oracle_job["grad_rho"])):
-        assert np.linalg.norm(got.cpu().numpy() - ref) <= 1e-6 * np.linalg.norm(ref)
