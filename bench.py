@@ -449,22 +449,26 @@ def serving_measure(n_requests, seed=4, n_sat=64, max_slots=6):
     srv = S.Server(max_slots=max_slots)
     srv.run(reqs, realtime=True)
     out = S.summarize(reqs)
-    # one request of each grid size alone: seconds per voxel-iteration of that size
-    alone = {}
+    # one request of each grid size alone (the first of that size in the stream, same medium and source):
+    # seconds per voxel-iteration of that size with nothing else on the GPU
+    alone, alone_status = {}, {}
     for r in reqs:
-        if r.shape in alone:
+        if r.shape in alone_status:
             continue
-        one = S.make_requests(n=1, seed=seed + 2000, device=dev)[0]
-        one.shape, one.src_pos, one.ppw, one.f_hz, one.seed = r.shape, r.src_pos, r.ppw, r.f_hz, r.seed
+        one = S.Request(rid=-1, arrival=0.0, shape=r.shape, ppw=r.ppw, seed=r.seed, src_pos=r.src_pos, f_hz=r.f_hz)
         one.problem = S.build_problem(one, device=dev)
         S.Server(max_slots=1).run([one], realtime=False)
-        alone[r.shape] = (one.done - one.admitted) / max(1, int(np.prod(r.shape)) * one.iters)
-    serial_s = sum(alone[r.shape] * int(np.prod(r.shape)) * r.iters for r in reqs)
-    vox_it = sum(int(np.prod(r.shape)) * r.iters for r in reqs)
+        alone_status["x".join(map(str, r.shape))] = one.status
+        if one.status == "CBS_OK" and one.iters > 0:
+            alone[r.shape] = (one.done - one.admitted) / (int(np.prod(r.shape)) * one.iters)
+    ok = [r for r in reqs if r.shape in alone]
+    serial_s = sum(alone[r.shape] * int(np.prod(r.shape)) * r.iters for r in ok)
+    vox_it = sum(int(np.prod(r.shape)) * r.iters for r in ok)
     out.update({"arrival_rate_req_s": rate, "saturated_req_s": sat["throughput_req_s"], "saturation_burst": n_sat,
                 "max_concurrent": srv.max_concurrent, "max_slots": max_slots,
-                "one_at_a_time_voxel_iters_per_s": vox_it / serial_s,
+                "one_at_a_time_voxel_iters_per_s": vox_it / serial_s if serial_s > 0 else None,
                 "alone_voxel_iters_per_s": {"x".join(map(str, k)): 1.0 / v for k, v in alone.items()},
+                "alone_status": alone_status,
                 "grids": "64^3/96^3/128^3/192^3, 512^2/1024^2/2048^2; 250 kHz/500 kHz/1 MHz; FP32+refine to 1e-6"})
     return out
 
