@@ -417,17 +417,23 @@ def run_kernels(args):
     from paper_2507_16087_gb300 import cbs, workloads as W
 
     dev = torch.device("cuda", 0)
-    p = W.sphere_128()
+    if args.shape:
+        shape = tuple(int(v) for v in args.shape.split(","))
+        p = W.smooth_random_medium(shape, seed=1, n_abs=16)
+        p.source = W.point_source(shape, tuple(s // 3 for s in shape[::-1]))
+    else:
+        p = W.sphere_128()
     T = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
     prec = "fp64" if args.precision == "fp64" else "fp32_refine"
     s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max, precision=prec, tol=TOL)
     src = T(p.source, torch.complex128)
-    y = torch.zeros((4,) + p.shape, dtype=torch.complex128, device=dev)
+    y = torch.zeros((p.ndim + 1,) + p.shape, dtype=torch.complex128, device=dev)
     s.scale_source(src, y)
     x = torch.zeros_like(y)
     kt = s.time_kernels(y, x, args.iters)
     s.destroy()
-    print(json.dumps({"mode": "kernels", "precision": prec, "iters": args.iters, "kernel_ms": kt}))
+    print(json.dumps({"mode": "kernels", "shape": list(p.shape), "precision": prec, "iters": args.iters,
+                      "kernel_ms": kt, "iteration_ms": sum(kt.values())}))
     return 0
 
 
@@ -457,6 +463,7 @@ def serving_measure(n_requests, seed=4, n_sat=64, max_slots=6):
             continue
         one = S.Request(rid=-1, arrival=0.0, shape=r.shape, ppw=r.ppw, seed=r.seed, src_pos=r.src_pos, f_hz=r.f_hz)
         one.problem = S.build_problem(one, device=dev)
+        torch.cuda.synchronize()
         S.Server(max_slots=1).run([one], realtime=False)
         alone_status["x".join(map(str, r.shape))] = one.status
         if one.status == "CBS_OK" and one.iters > 0:
@@ -615,6 +622,7 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--shape", default="", help="kernels mode: numpy grid shape, e.g. 2048,2048 (default: the 128^3 sphere)")
     args = ap.parse_args()
     if args.mode == "kernels":
         return run_kernels(args)

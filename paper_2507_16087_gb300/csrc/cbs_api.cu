@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "cbs.h"
@@ -32,6 +33,34 @@ using namespace cbs;
 namespace {
 
 constexpr int kHostBuf = 8192;  // pinned host doubles
+
+// Pinned host buffers for the norm read-backs, kept in a process-wide pool and never freed while the library is
+// loaded: cudaFreeHost may synchronise the whole device, which would stall the streams of every other solver
+// running when one solver is destroyed (the serving loop creates and destroys solvers while others run).
+std::mutex g_pinned_mu;
+std::vector<double*> g_pinned_free;
+
+double* pinned_get()
+{
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            double* p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    double* p = nullptr;
+    if (cudaMallocHost(&p, kHostBuf * sizeof(double)) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void pinned_put(double* p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
 constexpr int kSetupThreads = 256;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
@@ -1265,7 +1294,7 @@ void solver_destroy(cbs_solver* s)
     }
     if (s->fft_plan_ok) cufftDestroy(s->fft_plan);
     for (void* p : s->allocs) dev_put(s, p);
-    if (s->host_red) cudaFreeHost(s->host_red);
+    pinned_put(s->host_red);
     if (s->ev_user) cudaEventDestroy(s->ev_user);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
@@ -1326,7 +1355,8 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
         CUDA_TRY(cudaEventCreateWithFlags(&s->ev_user, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreate(&s->ev0));
         CUDA_TRY(cudaEventCreate(&s->ev1));
-        CUDA_TRY(cudaMallocHost(&s->host_red, kHostBuf * sizeof(double)));
+        s->host_red = pinned_get();
+        if (!s->host_red) throw CudaError{cudaErrorMemoryAllocation, "cudaMallocHost", __LINE__};
         TRACE("create: begin_call");
         begin_call(s);
         TRACE("create: tables");

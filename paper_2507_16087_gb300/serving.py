@@ -57,6 +57,7 @@ class Request:
     residual: float = math.nan
     status: str = ""
     result: object = None          # pressure component (torch tensor on the host) when keep_results
+    ready: object = None           # CUDA event recorded after `problem` was made (torch.cuda.Event), or None
 
 
 def make_requests(n=256, seed=4, rate=None, sizes3d=(64, 96, 128, 192), sizes2d=(512, 1024, 2048), n_abs=16,
@@ -79,8 +80,18 @@ def make_requests(n=256, seed=4, rate=None, sizes3d=(64, 96, 128, 192), sizes2d=
         r = Request(rid=i, arrival=t, shape=shape, ppw=ppw, seed=int(rng.integers(0, 2 ** 31)), src_pos=pos, f_hz=f)
         if build:
             r.problem = build_problem(r, n_abs, device)
+            r.ready = _record_ready(device)
         reqs.append(r)
     return reqs
+
+
+def _record_ready(device=None):
+    """An event on the current stream after the work enqueued so far (the medium just made)."""
+    import torch
+
+    ev = torch.cuda.Event()
+    ev.record(torch.cuda.current_stream(device))
+    return ev
 
 
 def build_problem(r: Request, n_abs=16, device=None) -> W.Problem:
@@ -94,13 +105,14 @@ class Server:
     """Admission by slots and free HBM; one worker thread per running request."""
 
     def __init__(self, max_slots=6, reserve_bytes=8 << 30, tol=1e-6, precision="fp32_refine", keep_results=False,
-                 check_every=50):
+                 check_every=50, allocator="torch"):
         self.max_slots = max_slots
         self.reserve = reserve_bytes
         self.tol = tol
         self.precision = precision
         self.keep = keep_results
         self.check_every = check_every
+        self.allocator = allocator
         self._lock = threading.Condition()
         self._running = 0
         self._reserved = 0
@@ -120,6 +132,13 @@ class Server:
         stream = torch.cuda.Stream(device=dev)
         try:
             with torch.cuda.stream(stream):
+                if r.problem is not None:
+                    # the medium was made on another stream (torch's streams do not wait for each other): order
+                    # this request's work after it
+                    if r.ready is not None:
+                        stream.wait_event(r.ready)
+                    else:
+                        stream.wait_stream(torch.cuda.default_stream(dev))
                 p = r.problem if r.problem is not None else build_problem(r, device=dev)
                 c0, rho, al = p.c0, p.rho, p.alpha
                 C = len(r.shape) + 1
@@ -127,8 +146,11 @@ class Server:
                 src[(C - 1,) + tuple(r.src_pos[::-1])] = 1.0
                 field = torch.empty_like(src)
                 stream.synchronize()
+                # the solver's arrays come from torch's caching allocator: cudaMalloc / cudaFree can synchronise
+                # the device and would stall the other requests' streams at every admission and completion
                 s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision=self.precision,
-                                      tol=self.tol, check_every=self.check_every, stream=stream)
+                                      tol=self.tol, check_every=self.check_every, stream=stream,
+                                      allocator=self.allocator)
                 info = s.solve_forward(src, field, allow_noconv=True)
                 s.destroy()
                 if self.keep:
