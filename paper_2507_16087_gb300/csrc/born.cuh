@@ -490,6 +490,28 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// the same copy with an L2 eviction-priority hint (an L2 cache policy made by createpolicy)
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+// L2 policies: data read once (evicted first) and data the next kernel reads again (evicted last)
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
 {
     uint32_t ok;
@@ -514,6 +536,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
         if (mbar_try_wait(bar, phase)) return true;
     return false;
 }
+
+// orders this thread's shared-memory accesses before later bulk / tensor copies that read or overwrite the buffer
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <typename R, int NX, int RX> struct BulkCfg {
     using Rc = RowCfg<R, NX, RX>;
@@ -689,33 +714,41 @@ k_rows_inv_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, cplx<R>* __restric
 // iteration's w = FFT_x(B x + y) is written in place of the consumed w.  Per
 // voxel this moves w, x, y and the medium in and x, w out, instead of also
 // reading x and the medium a second time.  Norm partials as in k_rows_inv_bulk.
-template <typename R, int NX, int RX> struct FusedCfg {
+// VAR (measured variants): bit 0 twiddles read from the table instead of registers, bit 1 y staged into w's
+// buffer once the inverse transform is done (two field buffers instead of three), bit 2 L2 hints on the
+// copies (x, y and the medium read once: evict first; w: evict last); bits 0 and 1: four blocks an SM
+template <typename R, int NX, int RX, int VAR = 0> struct FusedCfg {
     using Rc = RowCfg<R, NX, RX>;
+    static constexpr bool NOTC = (VAR & 1) != 0;
+    static constexpr bool YWS = (VAR & 2) != 0;
+    static constexpr bool HINT = (VAR & 4) != 0;
     static constexpr int ROWS = Rc::ROWS;
     static constexpr int T = Rc::T;
     static constexpr int THREADS = Rc::THREADS;
     static constexpr int ELEMS = ROWS * NX;
-    // w (also the exchange), x, y, medium m0, m1, three mbarriers
-    static constexpr size_t SMEM = 3 * (size_t)ELEMS * sizeof(cplx<R>) + 2 * (size_t)ELEMS * sizeof(R) + 32;
+    static constexpr int NF = YWS ? 2 : 3;  // field buffers: w (also the exchange and, with YWS, y), x[, y]
+    // field buffers, medium m0, m1, three mbarriers
+    static constexpr size_t SMEM = NF * (size_t)ELEMS * sizeof(cplx<R>) + 2 * (size_t)ELEMS * sizeof(R) + 32;
+    static constexpr int MINB = sizeof(R) == 4 ? ((VAR & 3) == 3 ? 4 : 3) : 1;
     static constexpr bool OK = (Rc::SL == NX) && ((size_t)ELEMS * sizeof(R)) % 16 == 0;
 };
 
-template <typename R, int NX, int RX>
-__global__ void __launch_bounds__(FusedCfg<R, NX, RX>::THREADS, sizeof(R) == 4 ? 3 : 1)
+template <typename R, int NX, int RX, int VAR = 0>
+__global__ void __launch_bounds__(FusedCfg<R, NX, RX, VAR>::THREADS, FusedCfg<R, NX, RX, VAR>::MINB)
 k_rows_inv_fwd_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>* __restrict__ y,
                     cplx<R>* __restrict__ w, const cplx<R>* __restrict__ tw, int adj, R nu,
                     double* __restrict__ partials, int* err)
 {
     using CT = cplx<R>;
-    using Cfg = FusedCfg<R, NX, RX>;
+    using Cfg = FusedCfg<R, NX, RX, VAR>;
     constexpr int T = Cfg::T;
     constexpr int E = Cfg::ELEMS;
     constexpr int np = plan_npass(NX, RX);
     extern __shared__ __align__(128) unsigned char smraw[];
     CT* ws = reinterpret_cast<CT*>(smraw);
     CT* xs = ws + E;
-    CT* ys = xs + E;
-    R* m0s = reinterpret_cast<R*>(ys + E);
+    CT* ys = Cfg::YWS ? ws : xs + E;
+    R* m0s = reinterpret_cast<R*>(xs + (Cfg::NF - 1) * E);
     R* m1s = m0s + E;
     uint64_t* bar = reinterpret_cast<uint64_t*>(m1s + E);
     const int lr = threadIdx.x / T, t = threadIdx.x % T;
@@ -736,16 +769,30 @@ k_rows_inv_fwd_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>*
     if (threadIdx.x == 0) {
         const uint32_t fb = E * sizeof(CT), mb = E * sizeof(R);
         mbar_expect_tx(bar, fb);
-        bulk_g2s(ws, w + fbase0, fb, bar);
         mbar_expect_tx(bar + 1, fb + (pres ? 2 : 1) * mb);
-        bulk_g2s(xs, x + fbase0, fb, bar + 1);
-        bulk_g2s(m0s, m0g, mb, bar + 1);
-        if (pres) bulk_g2s(m1s, M.et + vbase0, mb, bar + 1);
-        mbar_expect_tx(bar + 2, fb);
-        bulk_g2s(ys, y + fbase0, fb, bar + 2);
+        if constexpr (Cfg::HINT) {
+            const uint64_t once = l2_policy_evict_first(), again = l2_policy_evict_last();
+            bulk_g2s_hint(ws, w + fbase0, fb, bar, again);
+            bulk_g2s_hint(xs, x + fbase0, fb, bar + 1, once);
+            bulk_g2s_hint(m0s, m0g, mb, bar + 1, once);
+            if (pres) bulk_g2s_hint(m1s, M.et + vbase0, mb, bar + 1, once);
+            if constexpr (!Cfg::YWS) {
+                mbar_expect_tx(bar + 2, fb);
+                bulk_g2s_hint(ys, y + fbase0, fb, bar + 2, once);
+            }
+        } else {
+            bulk_g2s(ws, w + fbase0, fb, bar);
+            bulk_g2s(xs, x + fbase0, fb, bar + 1);
+            bulk_g2s(m0s, m0g, mb, bar + 1);
+            if (pres) bulk_g2s(m1s, M.et + vbase0, mb, bar + 1);
+            if constexpr (!Cfg::YWS) {
+                mbar_expect_tx(bar + 2, fb);
+                bulk_g2s(ys, y + fbase0, fb, bar + 2);
+            }
+        }
     }
     TwCache<NX, RX, CT> tc;
-    tw_load<NX, RX, T>(tc, t, tw);
+    if constexpr (!Cfg::NOTC) tw_load<NX, RX, T>(tc, t, tw);
     const long long rest = rest0 + lr;
     const int i1 = (int)(rest % d.n1), i2 = (int)(rest / d.n1);
     const RowB<R> rb = row_B(M, d.D, c, i1, i2, rest * NX);
@@ -761,8 +808,17 @@ k_rows_inv_fwd_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>*
     CT v[RX];
 #pragma unroll
     for (int s = 0; s < RX; ++s) v[s] = ws[lr * NX + t + T * slot_q<NX, RX, 0>(s)];
-    fft_run<NX, RX, +1, true>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
+    fft_run<NX, RX, +1, true, 0, !Cfg::NOTC>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
+    // (the barrier below also ends every read of w's buffer by the inverse transform)
     if (__syncthreads_or(!mbar_wait_bounded(bar + 1, 0))) { fail(1); return; }
+    if constexpr (Cfg::YWS) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();  // the generic-proxy reads of the buffer come before the copy's writes
+            mbar_expect_tx(bar + 2, E * sizeof(CT));
+            if constexpr (Cfg::HINT) bulk_g2s_hint(ys, y + fbase0, E * sizeof(CT), bar + 2, l2_policy_evict_first());
+            else bulk_g2s(ys, y + fbase0, E * sizeof(CT), bar + 2);
+        }
+    }
     R s0 = (R)0, s1 = (R)0;
     const long long fbase = fbase0 + (long long)lr * NX;
 #pragma unroll
@@ -785,7 +841,8 @@ k_rows_inv_fwd_bulk(Dims d, Medium<R> M, cplx<R>* __restrict__ x, const cplx<R>*
     for (int s = 0; s < RX; ++s) v[s] = cadd(v[s], ys[lr * NX + t + T * slot_q<NX, RX, np>(s)]);
     // same positions, entry order of the forward transform
     permute_slots<NX, RX, np, 0>(v);
-    fft_run<NX, RX, -1, true>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
+    if constexpr (Cfg::YWS) __syncthreads();  // every thread has read its y values from w's buffer
+    fft_run<NX, RX, -1, true, 0, !Cfg::NOTC>(v, ws + lr * NX, 1, t, tw, tc, RowSync<T>());
 #pragma unroll
     for (int s = 0; s < RX; ++s) w[fbase + t + T * slot_q<NX, RX, np>(s)] = v[s];
 }
@@ -809,8 +866,7 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void*
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // returns once the committed stores have finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// orders this thread's shared-memory writes before later tensor copies that read them
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 
 // ------------------------------------------------ last_symbol, tile-staged
 // The k_last_symbol step for 3D fields, with the block's data staged in shared

@@ -1533,6 +1533,8 @@ cbs_status solver_create(const cbs_grid* grid, double dx, double omega, const do
             const bool off = std::getenv("CBS_NO_FUSED_ROWS") != nullptr;
             s->P64.fused_rows = !off && fused_rows_ok<double>(s->P64);
             s->P32.fused_rows = !off && o.precision != CBS_FP64 && fused_rows_ok<float>(s->P32);
+            const char* v = std::getenv("CBS_FUSED_VAR");  // measured variants of the fused row kernel
+            s->P32.fused_var = (v != nullptr && ((v[0] >= '0' && v[0] <= '3') || v[0] == '6')) ? v[0] - '0' : -1;
         }
         CUDA_TRY(cudaEventRecord(s->ev1, s->st));
         CUDA_TRY(cudaStreamSynchronize(s->st));

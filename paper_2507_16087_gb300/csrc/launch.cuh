@@ -76,6 +76,7 @@ template <typename R> struct Plan {
     bool last_cluster = false;  // float32 last-axis step on a cluster of C CTAs (see last_cluster_ok)
     int plane_cl = 2;           // CTAs per x-y plane of the plane kernels (2 or 4)
     bool fused_rows = false;    // update + next forward row transform in one kernel (see fused_rows_ok)
+    int fused_var = -1;         // variant of the fused row kernel (float32, 128- to 512-point rows); -1: default
 };
 
 // x-y plane kernels: 3D float32 with n0, n1 in {32, 64, 128}; one CTA pair per (component, z) plane.
@@ -183,6 +184,21 @@ template <typename R> inline bool fused_rows_ok(const Plan<R>& P)
     }
 }
 
+template <typename R, int N, int VAR> cudaError_t rows_inv_fwd_var(const Plan<R>& P, cplx<R>* x, const cplx<R>* y,
+                                                                   cplx<R>* w, int adj, R nu, double* partials,
+                                                                   cudaStream_t st)
+{
+    constexpr int RX = r_rows<R>(N);
+    using Cfg = FusedCfg<R, N, RX, VAR>;
+    auto kern = k_rows_inv_fwd_bulk<R, N, RX, VAR>;
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (attr != cudaSuccess) return attr;
+    const long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
+    kern<<<(unsigned)(rows / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, st>>>(P.d, P.M, x, y, w, P.tw[0], adj, nu, partials,
+                                                                        P.err);
+    return cudaGetLastError();
+}
+
 template <typename R, int N> cudaError_t rows_inv_fwd_n(const Plan<R>& P, cplx<R>* x, const cplx<R>* y, cplx<R>* w,
                                                         int adj, R nu, double* partials, cudaStream_t st)
 {
@@ -190,13 +206,20 @@ template <typename R, int N> cudaError_t rows_inv_fwd_n(const Plan<R>& P, cplx<R
     using Cfg = FusedCfg<R, N, RX>;
     if constexpr (Cfg::OK) {
         if (!fused_rows_ok_n<R, N>(P)) return cudaErrorNotSupported;
-        auto kern = k_rows_inv_fwd_bulk<R, N, RX>;
-        static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-        if (attr != cudaSuccess) return attr;
-        const long long rows = (long long)(P.d.D + 1) * (P.d.N / N);
-        kern<<<(unsigned)(rows / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, st>>>(P.d, P.M, x, y, w, P.tw[0], adj, nu, partials,
-                                                                            P.err);
-        return cudaGetLastError();
+        if constexpr (sizeof(R) == 4 && (N == 128 || N == 256 || N == 512)) {
+            // default: y staged into the transform's buffer (measured: 128^3 59.6 instead of 64.0 us, 512^3 4.06
+            // instead of 4.30 ms; 256^3 480 instead of 502 us with the four-block variant); L2 hints on the copies
+            // gained nothing with the persisting window on w
+            const int var = P.fused_var >= 0 ? P.fused_var : 2;
+            switch (var) {
+            case 1: return rows_inv_fwd_var<R, N, 1>(P, x, y, w, adj, nu, partials, st);
+            case 2: return rows_inv_fwd_var<R, N, 2>(P, x, y, w, adj, nu, partials, st);
+            case 3: return rows_inv_fwd_var<R, N, 3>(P, x, y, w, adj, nu, partials, st);
+            case 6: return rows_inv_fwd_var<R, N, 6>(P, x, y, w, adj, nu, partials, st);
+            default: break;
+            }
+        }
+        return rows_inv_fwd_var<R, N, 0>(P, x, y, w, adj, nu, partials, st);
     } else {
         return cudaErrorNotSupported;
     }

@@ -493,3 +493,25 @@ def test_collocated_grid_adjoint_matches_oracle(shape):
     s.born_iterate(T(y), x, 30, adjoint=True)
     xr, _ = P.iterate(y, n_iter=30, nu=0.5, adjoint=True)
     assert rel(x.cpu().numpy(), xr) <= 1e-11
+
+
+@pytest.mark.parametrize("var", ["0", "1", "2", "3", "6"])
+@pytest.mark.parametrize("shape", [(16, 24, 128), (8, 16, 512), (24, 256)])
+def test_fused_row_kernel_variants_match_default_and_oracle(var, shape, monkeypatch):
+    """The fused update + next forward row kernel's variants (three field buffers, twiddles from the table, y
+    staged in the transform's buffer, the last two together) give the default kernel's float32 Born iterations
+    to rounding and match the oracle."""
+    monkeypatch.setenv("CBS_FUSED_VAR", var)
+    _, s, P = make(shape, seed=48, precision="fp32")
+    monkeypatch.delenv("CBS_FUSED_VAR")
+    _, s_ref, _ = make(shape, seed=48, precision="fp32")
+    for adjoint in (False, True):
+        y = P.scale_source(W.random_source(shape, 49), adjoint)
+        x = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+        x_ref = torch.zeros_like(x)
+        inc = s.born_iterate(T(y), x, 12, adjoint)
+        inc_ref = s_ref.born_iterate(T(y), x_ref, 12, adjoint)
+        assert rel(x.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-6
+        assert np.allclose(inc, inc_ref, rtol=1e-5, atol=0)
+        xr, _ = P.iterate(y, n_iter=12, nu=0.5, adjoint=adjoint)
+        assert rel(x.cpu().numpy(), xr) <= 1e-5
