@@ -353,6 +353,32 @@ def run_gpu(args):
             "iteration_frac": sum(bpv[k] for k in kt) * Nv / (iter_ms / 1e3) / 1e9 / peak,
             "iteration_frac_compulsory": 108 * Nv / (iter_ms / 1e3) / 1e9 / peak}
 
+    # the largest configuration's grid (512^3, float32 iterations): per-kernel event times of a few iterations
+    # on a sphere-inclusion medium (an iteration's time does not depend on the medium), against the same byte model
+    large = None
+    if not args.no_large and rank == 0:
+        n = 512
+        pl = W.inclusion_medium((n, n, n), 120, 1800.0, 1300.0, 1.0, ppw=6.0, n_abs=24)
+        sl = cbs.solver_create(T(pl.c0), T(pl.rho), T(pl.alpha), pl.dx, pl.omega, pl.nabs, pl.gamma_max,
+                               precision="fp32_refine", **kw)
+        del pl
+        yl = torch.zeros((4, n, n, n), dtype=torch.complex128, device=dev)
+        yl[3, n // 2, n // 2, 30] = 1.0
+        xl = torch.zeros_like(yl)
+        sl.time_kernels(yl, xl, 1)
+        ktl = sl.time_kernels(yl, xl, 3)
+        sl.destroy()
+        del yl, xl
+        torch.cuda.empty_cache()
+        it_ms = sum(ktl.values())
+        nl = float(n) ** 3
+        top_l = max(ktl, key=lambda k: ktl[k])
+        large = {"shape": [n, n, n], "kernel_ms": ktl, "iteration_ms": it_ms,
+                 "voxel_iters_per_s": nl / (it_ms / 1e3),
+                 "iteration_frac": sum(bpv[k] for k in ktl) * nl / (it_ms / 1e3) / 1e9 / peak,
+                 "per_kernel_frac": {k: bpv[k] * nl / (ktl[k] / 1e3) / 1e9 / peak for k in ktl},
+                 "top_kernel": top_l}
+
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     hc = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.c0, p.rho, p.alpha)]
     hs = torch.from_numpy(np.ascontiguousarray(p.source)).pin_memory()
@@ -377,7 +403,7 @@ def run_gpu(args):
 
     serving = None
     if args.serve_sample > 0:
-        serving = serving_measure(args.serve_sample, seed=4, n_sat=min(64, args.serve_sample), max_slots=args.slots)
+        serving = serving_measure(args.serve_sample, seed=4, max_slots=args.slots)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -401,7 +427,8 @@ def run_gpu(args):
                 "time_to_1e-6_ms": step_ms, "iters": float(np.mean(iters)),
                 "outer_iters": infos[-1]["outer_iters"], "rel_residual": infos[-1]["rel_residual"],
                 "setup_ms": infos[-1]["t_setup_ms"], "fp64": fp64, "roofline": roof, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "serving": serving, "cufft_baseline": cufft}
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "serving": serving, "cufft_baseline": cufft,
+                "large_grid": large}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -437,17 +464,18 @@ def run_kernels(args):
     return 0
 
 
-def serving_measure(n_requests, seed=4, n_sat=64, max_slots=6):
-    """Serving stream: the saturated throughput from a burst of n_sat requests of the same mix (all queued at
-    once), then n_requests Poisson arrivals at 0.8 x that rate; p50 / p99 latency over all of them and the
-    aggregate throughput.  Beside it, each grid size solved alone (one request per size, nothing else on the
-    GPU) gives the throughput a one-request-at-a-time server would reach on the same stream."""
+def serving_measure(n_requests, seed=4, n_sat=None, max_slots=6):
+    """Serving stream: the saturated throughput from the first n_sat requests of the same stream (all queued at
+    once; the whole stream by default), then the n_requests as Poisson arrivals at 0.8 x that rate; p50 / p99
+    latency over all of them and the aggregate throughput.  Beside it, each grid size solved alone (one request
+    per size, nothing else on the GPU) gives the throughput a one-request-at-a-time server would reach on the
+    same stream."""
     import torch
 
     from paper_2507_16087_gb300 import serving as S
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    burst = S.make_requests(n=n_sat, seed=seed + 1000, device=dev)
+    burst = S.make_requests(n=n_sat or n_requests, seed=seed, device=dev)
     S.Server(max_slots=max_slots).run(burst, realtime=False)
     sat = S.summarize(burst)
     rate = 0.8 * sat["throughput_req_s"]
@@ -481,7 +509,7 @@ def serving_measure(n_requests, seed=4, n_sat=64, max_slots=6):
 
 
 def run_serve(args):
-    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests, max_slots=args.slots)
+    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests or None, max_slots=args.slots)
     out["mode"] = "serve"
     print(json.dumps(out))
     return 0
@@ -614,9 +642,10 @@ def main():
     ap.add_argument("--nu", type=float, default=0.8)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 512^3 per-kernel timing leg")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "skull", "serve", "sweep", "cpu"])
     ap.add_argument("--requests", type=int, default=256)
-    ap.add_argument("--sat-requests", type=int, default=64)
+    ap.add_argument("--sat-requests", type=int, default=0, help="requests of the saturation burst (0: the whole stream)")
     ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--serve-sample", type=int, default=256)
     ap.add_argument("--n", type=int, default=512)

@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-ORDER = ("gradient64", "served", "sphere128")  # the order the tests that read them run in
+ORDER = ("sphere128", "gradient64", "served")  # the longest first: all three finish while the GPU tests run
 
 # the two served requests: (rid, numpy shape, medium seed, source (x, y[, z]), PPW, frequency)
 SERVED = ((1000, (64, 64, 64), 71, (30, 25, 40), 6.5, 5e5),

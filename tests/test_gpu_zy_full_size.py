@@ -39,6 +39,26 @@ def _cbs():
     return cbs
 
 
+@pytest.mark.oracle_job("sphere128")
+def test_sphere_128_fp32_refine_matches_converged_oracle(oracle_job):
+    """The 128^3 sphere workload at its full size: the FP32 + FP64-refinement solve to residual 1e-8 against
+    the float64 oracle converged to 1e-8 (both are within (condition) x residual of the discrete solution;
+    the mixed-precision bound is 1e-5).  The oracle solve (minutes of host time) runs in the background."""
+    cbs = _cbs()
+    p = W.sphere_128()
+    s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max,
+                          precision="fp32_refine", tol=1e-8, check_every=50)
+    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
+    info = s.solve_forward(T(p.source), field)
+    assert info["rel_residual"] <= 1e-8
+    got = field.cpu().numpy()
+    ref = oracle_job["field"]
+    assert float(oracle_job["residual"]) <= 1e-8
+    assert rel(got, ref) <= 1e-5
+    # the pressure alone (the quantity a user reads) meets the same bound
+    assert rel(got[3], ref[3]) <= 1e-5
+
+
 @pytest.mark.oracle_job("gradient64")
 def test_autograd_gradient_matches_oracle_64(oracle_job):
     """The layered-inversion medium at 64^3 (one source, 64 receivers, seeded receiver data): misfit and
@@ -84,23 +104,3 @@ def test_served_requests_match_oracle(oracle_job):
         assert r.status == "CBS_OK" and r.residual <= 1e-8, (r.rid, r.status, r.residual)
         assert float(oracle_job[f"res{r.rid}"]) <= 1e-9
         assert rel(r.result.numpy(), oracle_job[f"p{r.rid}"]) <= 1e-5, r.rid
-
-
-@pytest.mark.oracle_job("sphere128")
-def test_sphere_128_fp32_refine_matches_converged_oracle(oracle_job):
-    """The 128^3 sphere workload at its full size: the FP32 + FP64-refinement solve to residual 1e-8 against
-    the float64 oracle converged to 1e-8 (both are within (condition) x residual of the discrete solution;
-    the mixed-precision bound is 1e-5).  The oracle solve (minutes of host time) runs in the background."""
-    cbs = _cbs()
-    p = W.sphere_128()
-    s = cbs.solver_create(T(p.c0), T(p.rho), T(p.alpha), p.dx, p.omega, p.nabs, p.gamma_max,
-                          precision="fp32_refine", tol=1e-8, check_every=50)
-    field = torch.zeros(s.field_shape, dtype=torch.complex128, device=DEV)
-    info = s.solve_forward(T(p.source), field)
-    assert info["rel_residual"] <= 1e-8
-    got = field.cpu().numpy()
-    ref = oracle_job["field"]
-    assert float(oracle_job["residual"]) <= 1e-8
-    assert rel(got, ref) <= 1e-5
-    # the pressure alone (the quantity a user reads) meets the same bound
-    assert rel(got[3], ref[3]) <= 1e-5
