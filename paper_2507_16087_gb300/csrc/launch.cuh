@@ -13,15 +13,23 @@ namespace cbs {
 
 // Elements per thread of one transform (RX for row/axis kernels, RL for the
 // all-components pencil kernel, which keeps C transforms in registers).
-template <typename R> __host__ __device__ constexpr int r_rows(int n) { return (n % 3 == 0) ? 12 : 8; }
+// float32 rows of 128 and more points: 16 values a thread (radix-16 passes: 128 = 16*8, 2048 = 16*16*8), measured
+// on the fused row kernel 438.9 instead of 479.7 us at 256^3, 144.4 instead of 169.8 us at 2048^2, 3.94 instead of
+// 4.06 ms at 512^3 (59.7 either way at 128^3)
+template <typename R> __host__ __device__ constexpr int r_rows(int n)
+{
+    return (n % 3 == 0) ? 12 : ((sizeof(R) == 4 && n >= 128) ? 16 : 8);
+}
 // strided-axis transforms: 16 values per thread for float32 128 / 256 (two passes, radix 16 then 8 or 16)
 template <typename R> __host__ __device__ constexpr int r_axis(int n)
 {
     return (n % 3 == 0) ? 12 : ((sizeof(R) == 4 && (n == 128 || n == 256)) ? 16 : 8);
 }
-template <typename R> __host__ __device__ constexpr int r_last(int n)
+template <typename R> __host__ __device__ constexpr int r_last(int n, int c = 4)
 {
-    return sizeof(R) == 4 ? ((n % 3 == 0) ? 6 : 8) : ((n % 3 == 0) ? 6 : 4);
+    // float32 3D 3*2^k pencils of 96 and 192 points: 12 values a thread (passes 3,4,4,...) instead of 6
+    // (3,2,2,...): measured 174 instead of 224 us at 192^3, 22.6 instead of 26.7 us at 96^3
+    return sizeof(R) == 4 ? ((n % 3 == 0) ? ((c == 4 && n >= 96) ? 12 : 6) : 8) : ((n % 3 == 0) ? 6 : 4);
 }
 template <typename R> __host__ __device__ constexpr int cols_axis(int n)
 {
@@ -31,7 +39,8 @@ template <typename R> __host__ __device__ constexpr int cols_last(int n, int c)
 {
     if (sizeof(R) == 4 && c == 3 && n == 512) return 4;  // 2D: the grid is n0 / COLS blocks, keep it wide
     // float32 512: 8 columns (64-byte rows) measured 3.27 ms instead of 4.73 ms with 4 at 512^3; 16 columns at
-    // 256 measured slower than 8
+    // 256 measured slower than 8; 3D 96 / 192 with 12 values a thread: 32 / 16 columns (256 threads)
+    if (sizeof(R) == 4 && c == 4 && n % 3 == 0 && n >= 96) return n <= 96 ? 32 : 16;
     return sizeof(R) == 4 ? (n <= 128 ? 16 : (n <= 256 ? 8 : (n <= 512 ? 8 : (n <= 1024 ? 4 : 2))))
                           : (n <= 128 ? 8 : (n <= 256 ? 4 : (n <= 512 ? 2 : (n <= 1024 ? 2 : 1))));
 }
@@ -304,7 +313,7 @@ template <typename R, int N, int C> cudaError_t last_n(const Plan<R>& P, cplx<R>
             P.d.n0 % cols_tile<R>(N) == 0)
             return last_tile_n<R, N, C>(P, w, mode, st);
     }
-    constexpr int RL = r_last<R>(N);
+    constexpr int RL = r_last<R>(N, C);
     constexpr int COLS = cols_last<R>(N, C);
     constexpr int T = N / RL;
     const size_t smem = (size_t)C * N * COLS * sizeof(cplx<R>);

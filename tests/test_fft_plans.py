@@ -23,8 +23,8 @@ using namespace cbs;
 extern "C" void r_choices(int n, int* out) {
     out[0] = r_rows<float>(n);  out[1] = r_rows<double>(n);
     out[2] = r_axis<float>(n);  out[3] = r_axis<double>(n);
-    out[4] = r_last<float>(n);  out[5] = r_last<double>(n);
-    out[6] = r_tile<float>(n);
+    out[4] = r_last<float>(n, 4);  out[5] = r_last<double>(n, 4);
+    out[6] = r_tile<float>(n);     out[7] = r_last<float>(n, 3);  out[8] = r_last<double>(n, 3);
 }
 extern "C" int npass(int n, int r) { return plan_npass(n, r); }
 extern "C" int radix(int n, int r, int p) { return plan_radix(n, r, p); }
@@ -77,7 +77,7 @@ def lib():
 def _pairs(L):
     out = set()
     for n in SIZES:
-        rc = np.zeros(7, dtype=np.int32)
+        rc = np.zeros(9, dtype=np.int32)
         L.r_choices(n, rc.ctypes.data)
         out |= {(n, int(r)) for r in rc}
         if n in (32, 64, 128):
