@@ -174,8 +174,9 @@ def sources_hash() -> str:
 
     d = os.path.join(ROOT, "paper_2507_16087_gb300", "csrc")
     h = hashlib.sha256()
+    off_path = {"measure.cu", "noalloc.cu"}  # not on the iteration's path
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh")) and f not in off_path:
             h.update(f.encode())
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(fh.read())
@@ -301,8 +302,17 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1)
+        # the float64 path is bound by the FP64 pipes: its flop rate (5 log2(N_v) flops per point per transform,
+        # forward and inverse, C components, plus ~100 for the symbol and the pointwise steps) against the
+        # measured FP64 FMA rate of this GPU
+        fp64_peak = cbs.fp64_rate()
+        flops_per_vi = 2 * 4 * 5 * np.log2(Nv) + 100
+        fp64_tflops = flops_per_vi * Nv * i64["iters"] / (t64 / 1e3) / 1e12
         fp64 = {"time_to_1e-6_ms": t64, "iters": i64["iters"], "rel_residual": i64["rel_residual"],
-                "voxel_iters_per_s": Nv * i64["iters"] / (t64 / 1e3)}
+                "voxel_iters_per_s": Nv * i64["iters"] / (t64 / 1e3),
+                "roofline": {"bound": "fp64", "achieved": fp64_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": fp64_tflops / fp64_peak, "peak_kind": "measured FP64 FMA chains (cbs_fp64_rate)",
+                             "flops_per_voxel_iter": flops_per_vi}}
 
     # per-kernel times (CUDA events on the solver's stream) for the roofline
     s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision="fp32_refine", **kw)

@@ -242,6 +242,14 @@ cbs_status cufft_baseline_iterate(cbs_solver* s, const void* y, void* x, int n_i
 enum { CBS_SELFTEST_BULK_TIMEOUT = 1 };
 cbs_status cbs_selftest(int which, int* result);
 
+/* Float64 arithmetic rate of the current device, for stating the float64 path against the roof that
+ * binds it (the paper has no counterpart; not on the solver's path).  Runs eight independent chains of
+ * double-precision fused multiply-adds in every thread of 16 blocks of 256 threads per SM and times the
+ * second of two launches with CUDA events on the default stream; *tflops = 2 * FMAs / time / 1e12.
+ * Allocates and frees 8 bytes of device memory.  CBS_EINVAL for a NULL pointer, CBS_ECUDA / CBS_ENOMEM
+ * when a CUDA call fails. */
+cbs_status cbs_fp64_rate(double* tflops);
+
 void solver_destroy(cbs_solver* s);
 
 /* Message of the last failure on this solver (or of the last failed

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcbs_gb300.so")
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "cbs_api.cu", "noalloc.cu"]
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "cbs_api.cu", "noalloc.cu", "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -61,7 +61,7 @@ class cbs_info(ctypes.Structure):
 EXPORTS = ("solver_create", "solve_forward", "solve_adjoint", "residual_norm", "born_iterate", "green_apply",
            "operator_apply", "scale_source", "unscale_field", "solver_scalars", "solver_time_kernels",
            "solver_destroy", "cbs_last_error", "green_apply_noalloc", "medium_gradient", "cbs_selftest",
-           "cufft_baseline_iterate")
+           "cufft_baseline_iterate", "cbs_fp64_rate")
 
 _lock = threading.Lock()
 _lib = None
@@ -117,6 +117,8 @@ def load(path: str | None = None):
         lib.green_apply_noalloc.argtypes = [ctypes.POINTER(cbs_grid), D, ctypes.POINTER(D), V, V, I, V]
         lib.cbs_selftest.restype = S
         lib.cbs_selftest.argtypes = [I, ctypes.POINTER(I)]
+        lib.cbs_fp64_rate.restype = S
+        lib.cbs_fp64_rate.argtypes = [ctypes.POINTER(D)]
         lib.cufft_baseline_iterate.restype = S
         lib.cufft_baseline_iterate.argtypes = [V, V, V, I, I, ctypes.POINTER(D)]
         if path is None:
@@ -125,6 +127,16 @@ def load(path: str | None = None):
 
 
 CBS_SELFTEST_BULK_TIMEOUT = 1
+
+
+def fp64_rate() -> float:
+    """Measured float64 FMA rate of the current device in TFLOP/s (cbs_fp64_rate)."""
+    lib = load()
+    out = ctypes.c_double(0.0)
+    st = lib.cbs_fp64_rate(ctypes.byref(out))
+    if st != CBS_OK:
+        raise CBSError(st, "cbs_fp64_rate failed")
+    return float(out.value)
 
 
 def selftest_bulk_timeout() -> int:
