@@ -12,7 +12,7 @@ for _p in (ROOT, HERE):
     if _p not in sys.path:
         sys.path.insert(0, _p)
 
-_jobs = {"proc": None, "dir": None, "log": None}
+_jobs = {"procs": [], "dir": None, "logs": []}
 
 
 def pytest_configure(config):
@@ -23,15 +23,23 @@ def pytest_configure(config):
 
 
 def _start_oracle_jobs(names):
-    """One background interpreter runs the selected oracle jobs (seeded inputs only) while the tests run."""
+    """Background interpreters run the selected oracle jobs (seeded inputs only) while the tests run: one per
+    group of oracle_jobs.GROUPS, each with half the host's cores."""
     import oracle_jobs as OJ
 
-    order = [n for n in OJ.ORDER if n in names]
     d = tempfile.mkdtemp(prefix="cbs_oracle_jobs_")
-    log = open(os.path.join(d, "jobs.log"), "w")
-    _jobs["proc"] = subprocess.Popen([sys.executable, os.path.join(ROOT, "tests", "oracle_jobs.py"), d, *order],
-                                     stdout=log, stderr=subprocess.STDOUT, cwd=ROOT)
-    _jobs["dir"], _jobs["log"] = d, log
+    _jobs["dir"] = d
+    env = dict(os.environ)
+    env["OMP_NUM_THREADS"] = str(max(1, (os.cpu_count() or 2) // 2))
+    for gi, group in enumerate(OJ.GROUPS):
+        todo = [n for n in group if n in names]
+        if not todo:
+            continue
+        log = open(os.path.join(d, f"jobs{gi}.log"), "w")
+        _jobs["procs"].append(subprocess.Popen(
+            [sys.executable, os.path.join(ROOT, "tests", "oracle_jobs.py"), d, *todo],
+            stdout=log, stderr=subprocess.STDOUT, cwd=ROOT, env=env))
+        _jobs["logs"].append(log)
 
 
 def pytest_collection_modifyitems(config, items):
@@ -52,15 +60,15 @@ def pytest_collection_modifyitems(config, items):
 
 
 def pytest_unconfigure(config):
-    p = _jobs["proc"]
-    if p is not None and p.poll() is None:
-        p.terminate()
-        try:
-            p.wait(timeout=10)
-        except Exception:
-            p.kill()
-    if _jobs["log"] is not None:
-        _jobs["log"].close()
+    for p in _jobs["procs"]:
+        if p.poll() is None:
+            p.terminate()
+            try:
+                p.wait(timeout=10)
+            except Exception:
+                p.kill()
+    for log in _jobs["logs"]:
+        log.close()
 
 
 @pytest.fixture
@@ -75,10 +83,14 @@ def oracle_job(request):
     path = OJ.job_path(_jobs["dir"], name)
     t0 = time.time()
     while not os.path.exists(path):
-        p = _jobs["proc"]
-        if p.poll() is not None and not os.path.exists(path):
-            with open(os.path.join(_jobs["dir"], "jobs.log")) as f:
-                raise RuntimeError(f"oracle job {name} did not finish (exit {p.returncode}):\n{f.read()[-4000:]}")
+        if all(p.poll() is not None for p in _jobs["procs"]) and not os.path.exists(path):
+            text = ""
+            for gi in range(len(OJ.GROUPS)):
+                lp = os.path.join(_jobs["dir"], f"jobs{gi}.log")
+                if os.path.exists(lp):
+                    with open(lp) as f:
+                        text += f.read()[-2000:]
+            raise RuntimeError(f"oracle job {name} did not finish:\n{text}")
         if time.time() - t0 > 3600:
             raise TimeoutError(f"oracle job {name} still running after an hour")
         time.sleep(1.0)

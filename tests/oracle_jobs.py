@@ -2,10 +2,10 @@
 
 TEST INFRASTRUCTURE.  Each job needs only seeded synthetic inputs (workloads,
 the oracle itself), never a result of the CUDA path, so it can run in a
-background process while the GPU tests run; ``tests/conftest.py`` starts one
-such process (a fresh interpreter) when a test that needs a job is selected,
-and the ``oracle_job`` fixture waits for the job's file.  Jobs run one after
-the other in the order of ``ORDER``.
+background process while the GPU tests run; ``tests/conftest.py`` starts such
+processes (fresh interpreters) when a test that needs a job is selected,
+and the ``oracle_job`` fixture waits for the job's file.  The jobs of one group
+of ``GROUPS`` run one after the other; the groups run side by side.
 
   sphere128   the 128^3 sphere workload solved to a scaled residual of 1e-8
               (Algorithm 1, nu = 0.8): the reference for the FP32 + FP64
@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-ORDER = ("sphere128", "gradient64", "served")  # the longest first: all three finish while the GPU tests run
+# jobs in one group run one after the other in one background interpreter; the groups run side by side
+GROUPS = (("sphere128",), ("gradient64", "served"))
 
 # the two served requests: (rid, numpy shape, medium seed, source (x, y[, z]), PPW, frequency)
 SERVED = ((1000, (64, 64, 64), 71, (30, 25, 40), 6.5, 5e5),
