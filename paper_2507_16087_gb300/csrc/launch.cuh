@@ -15,15 +15,17 @@ namespace cbs {
 // all-components pencil kernel, which keeps C transforms in registers).
 // float32 rows of 128 and more points: 16 values a thread (radix-16 passes: 128 = 16*8, 2048 = 16*16*8), measured
 // on the fused row kernel 438.9 instead of 479.7 us at 256^3, 144.4 instead of 169.8 us at 2048^2, 3.94 instead of
-// 4.06 ms at 512^3 (59.7 either way at 128^3)
+// 4.06 ms at 512^3 (59.7 either way at 128^3); float32 3*2^k rows of 192 and more points: 24 (passes 3, 8, 8),
+// 295 instead of 308 us at 192^3
 template <typename R> __host__ __device__ constexpr int r_rows(int n)
 {
-    return (n % 3 == 0) ? 12 : ((sizeof(R) == 4 && n >= 128) ? 16 : 8);
+    return (n % 3 == 0) ? ((sizeof(R) == 4 && n >= 192) ? 24 : 12) : ((sizeof(R) == 4 && n >= 128) ? 16 : 8);
 }
-// strided-axis transforms: 16 values per thread for float32 128 / 256 (two passes, radix 16 then 8 or 16)
+// strided-axis transforms: 16 values per thread for float32 128 / 256 (two passes, radix 16 then 8 or 16) and 512
+// (16, 16, 2: 1.52 instead of 1.94 ms at 512^3, 8 columns; 16 columns measured 2.27 ms)
 template <typename R> __host__ __device__ constexpr int r_axis(int n)
 {
-    return (n % 3 == 0) ? 12 : ((sizeof(R) == 4 && (n == 128 || n == 256)) ? 16 : 8);
+    return (n % 3 == 0) ? 12 : ((sizeof(R) == 4 && (n == 128 || n == 256 || n == 512)) ? 16 : 8);
 }
 template <typename R> __host__ __device__ constexpr int r_last(int n, int c = 4)
 {

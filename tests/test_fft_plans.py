@@ -44,7 +44,7 @@ template <int N, int R> int fill(int* sq, int* qs) {
 #define CASE_R(N) \
     if (r == 4) return fill<N, 4>(sq, qs); if (r == 6) return fill<N, 6>(sq, qs); \
     if (r == 8) return fill<N, 8>(sq, qs); if (r == 12) return fill<N, 12>(sq, qs); \
-    if (r == 16) return fill<N, 16>(sq, qs); return -2;
+    if (r == 16) return fill<N, 16>(sq, qs); if (r == 24) return fill<N, 24>(sq, qs); return -2;
 extern "C" int slots(int n, int r, int* sq, int* qs) {
     switch (n) {
 #define CBS_CASE(N) case N: { CASE_R(N) }
