@@ -1087,6 +1087,13 @@ double2 support_mec(cbs_solver* s, const double2* vals, long long n)
     return mec_centre(pts);
 }
 
+// Solvers holding a persisting-L2 window, and the context's persisting-L2 limit before the first of them
+// raised it: when the last one is destroyed the persisting lines are reset and the limit restored, so the
+// set-aside part of L2 does not stay reserved for kernels that no longer run.
+std::mutex g_l2_mu;
+int g_l2_users = 0;
+size_t g_l2_limit0 = 0;
+
 // Keep the float32 work array resident in L2 across the five kernels of an
 // iteration: an access-policy window marks it persisting (the others stream).
 // The persisting-L2 limit is a property of this process's CUDA context (it
@@ -1104,9 +1111,15 @@ void set_l2_window(cbs_solver* s, void* base, size_t bytes)
     if (bytes > (size_t)max_persist || bytes > (size_t)max_window) return;
     const size_t win = bytes;
     size_t cur = 0;
-    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
-    if (cur < std::min(win, (size_t)max_persist)) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(win, (size_t)max_persist));
-    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    {
+        std::lock_guard<std::mutex> lk(g_l2_mu);
+        cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+        if (g_l2_users == 0) g_l2_limit0 = cur;
+        ++g_l2_users;
+        if (cur < std::min(win, (size_t)max_persist))
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(win, (size_t)max_persist));
+        cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    }
     cudaStreamAttrValue v{};
     v.accessPolicyWindow.base_ptr = base;
     v.accessPolicyWindow.num_bytes = win;
@@ -1288,6 +1301,16 @@ void solver_destroy(cbs_solver* s)
 {
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
+    // the last solver holding a window resets the persisting lines and restores the persisting-L2 limit, so the
+    // set-aside part of L2 is not kept from the process's later kernels
+    if (s->l2_window_set) {
+        std::lock_guard<std::mutex> lk(g_l2_mu);
+        if (--g_l2_users == 0) {
+            cudaCtxResetPersistingL2Cache();
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_limit0);
+        }
+        cudaGetLastError();
+    }
     for (int a = 0; a < 2; ++a) {
         if (s->graph64[a]) cudaGraphExecDestroy(s->graph64[a]);
         if (s->graph32[a]) cudaGraphExecDestroy(s->graph32[a]);

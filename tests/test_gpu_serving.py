@@ -56,3 +56,13 @@ def test_footprint_admission_estimate_covers_solver_memory():
     assert used <= S.footprint_bytes(shape)
     s.destroy()
     del src, field
+
+
+def test_freshly_made_media_are_ready_when_served():
+    """A request's medium is made on the device just before it is served (another stream): the solve is ordered
+    after it, so the largest grids' media are complete when the solver reads them."""
+    from paper_2507_16087_gb300 import serving as S
+
+    reqs = S.make_requests(n=4, seed=21, sizes3d=(192,), sizes2d=(2048,), device="cuda:0")
+    S.Server(max_slots=4).run(reqs, realtime=False)
+    assert [r.status for r in reqs] == ["CBS_OK"] * 4, [r.status for r in reqs]
