@@ -195,7 +195,8 @@ cbs_status solver_scalars(const cbs_solver* s, double* out);
  * (the per-block norm reduction, one launch per check_every iterations, is not
  * included),
  * measured with CUDA events on the solver's stream over n_iter iterations
- * (scaled iterate and source taken as given, updated in place).  names
+ * after one untimed iteration (scaled iterate and source taken as given,
+ * updated in place by all n_iter + 1 iterations).  names
  * receives up to max_k NUL-separated kernel names; ms receives one time per
  * kernel; *nk the kernel count. */
 cbs_status solver_time_kernels(cbs_solver* s, const void* y, void* x, int n_iter, char* names, int names_len,

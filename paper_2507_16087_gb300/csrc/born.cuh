@@ -1066,7 +1066,8 @@ k_axis_fft_pipe(const __grid_constant__ CUtensorMap tmap, Dims d, cplx<R>* __res
         const long long base = zc * (long long)d.n0 * d.n1 + xb * COLS + col;
 #pragma unroll
         for (int s = 0; s < RA; ++s) w[base + (long long)(t + T * slot_q<NA, RA, np>(s)) * d.n0] = v[s];
-        __syncthreads();  // every thread is done with this stage (inputs and exchanges)
+        fence_proxy_async_smem();  // this thread's exchange writes to the stage come before the next copy into it
+        __syncthreads();           // every thread is done with this stage (inputs and exchanges)
         if (threadIdx.x == 0 && tile + 2LL * gridDim.x < ntiles) issue(tile + 2LL * gridDim.x, st);
     }
 }

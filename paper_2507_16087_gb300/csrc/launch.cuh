@@ -229,6 +229,11 @@ template <typename R, int N> cudaError_t rows_inv_fwd_n(const Plan<R>& P, cplx<R
             case 6: return rows_inv_fwd_var<R, N, 6>(P, x, y, w, adj, nu, partials, st);
             default: break;
             }
+        } else if constexpr (sizeof(R) == 4 && FusedCfg<R, N, RX, 2>::OK) {
+            // the other float32 row lengths (192, 1024, 2048): y staged into the transform's buffer too (measured
+            // 192^3 289 instead of 298 us, 1024^2 35.2 instead of 37.2 us, 2048^2 133.3 instead of 142.4 us);
+            // CBS_FUSED_VAR=0 keeps three field buffers
+            if (P.fused_var != 0) return rows_inv_fwd_var<R, N, 2>(P, x, y, w, adj, nu, partials, st);
         }
         return rows_inv_fwd_var<R, N, 0>(P, x, y, w, adj, nu, partials, st);
     } else {

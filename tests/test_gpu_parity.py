@@ -495,8 +495,13 @@ def test_collocated_grid_adjoint_matches_oracle(shape):
     assert rel(x.cpu().numpy(), xr) <= 1e-11
 
 
-@pytest.mark.parametrize("var", ["0", "1", "2", "3", "6"])
-@pytest.mark.parametrize("shape", [(16, 24, 128), (8, 16, 512), (24, 256)])
+_FUSED_VARIANTS = [(v, sh) for v in ("0", "1", "2", "3", "6") for sh in ((16, 24, 128), (8, 16, 512), (24, 256))]
+# the other float32 row lengths (192, 1024, 2048 points): three field
+# buffers against the default, y staged in the transform's buffer
+_FUSED_VARIANTS += [("0", sh) for sh in ((8, 12, 192), (8, 1024), (8, 2048))]
+
+
+@pytest.mark.parametrize("var,shape", _FUSED_VARIANTS)
 def test_fused_row_kernel_variants_match_default_and_oracle(var, shape, monkeypatch):
     """The fused update + next forward row kernel's variants (three field buffers, twiddles from the table, y
     staged in the transform's buffer, the last two together) give the default kernel's float32 Born iterations
