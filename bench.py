@@ -413,7 +413,8 @@ def run_gpu(args):
 
     serving = None
     if args.serve_sample > 0:
-        serving = serving_measure(args.serve_sample, seed=4, max_slots=args.slots)
+        serving = serving_measure(args.serve_sample, seed=4, max_slots=args.slots,
+                                  exclusive_voxels=args.serve_exclusive)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -474,23 +475,25 @@ def run_kernels(args):
     return 0
 
 
-def serving_measure(n_requests, seed=4, n_sat=None, max_slots=6):
+def serving_measure(n_requests, seed=4, n_sat=None, max_slots=6, exclusive_voxels=1 << 20):
     """Serving stream: the saturated throughput from the first n_sat requests of the same stream (all queued at
     once; the whole stream by default), then the n_requests as Poisson arrivals at 0.8 x that rate; p50 / p99
     latency over all of them and the aggregate throughput.  Beside it, each grid size solved alone (one request
     per size, nothing else on the GPU) gives the throughput a one-request-at-a-time server would reach on the
-    same stream."""
+    same stream; the saturated burst's own voxel-iteration rate is the concurrent server's capacity to set
+    beside it (the Poisson stream's aggregate is bounded by the offered load).  exclusive_voxels: the server runs
+    requests of at least that many voxels one at a time among themselves (None or 0: arrival order only)."""
     import torch
 
     from paper_2507_16087_gb300 import serving as S
 
     dev = torch.device("cuda", torch.cuda.current_device())
     burst = S.make_requests(n=n_sat or n_requests, seed=seed, device=dev)
-    S.Server(max_slots=max_slots).run(burst, realtime=False)
+    S.Server(max_slots=max_slots, exclusive_voxels=exclusive_voxels).run(burst, realtime=False)
     sat = S.summarize(burst)
     rate = 0.8 * sat["throughput_req_s"]
     reqs = S.make_requests(n=n_requests, seed=seed, rate=rate, device=dev)
-    srv = S.Server(max_slots=max_slots)
+    srv = S.Server(max_slots=max_slots, exclusive_voxels=exclusive_voxels)
     srv.run(reqs, realtime=True)
     out = S.summarize(reqs)
     # one request of each grid size alone (the first of that size in the stream, same medium and source):
@@ -510,7 +513,8 @@ def serving_measure(n_requests, seed=4, n_sat=None, max_slots=6):
     serial_s = sum(alone[r.shape] * int(np.prod(r.shape)) * r.iters for r in ok)
     vox_it = sum(int(np.prod(r.shape)) * r.iters for r in ok)
     out.update({"arrival_rate_req_s": rate, "saturated_req_s": sat["throughput_req_s"], "saturation_burst": n_sat,
-                "max_concurrent": srv.max_concurrent, "max_slots": max_slots,
+                "saturated_voxel_iters_per_s": sat["voxel_iters_per_s"],
+                "max_concurrent": srv.max_concurrent, "max_slots": max_slots, "exclusive_voxels": exclusive_voxels,
                 "one_at_a_time_voxel_iters_per_s": vox_it / serial_s if serial_s > 0 else None,
                 "alone_voxel_iters_per_s": {"x".join(map(str, k)): 1.0 / v for k, v in alone.items()},
                 "alone_status": alone_status,
@@ -519,7 +523,8 @@ def serving_measure(n_requests, seed=4, n_sat=None, max_slots=6):
 
 
 def run_serve(args):
-    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests or None, max_slots=args.slots)
+    out = serving_measure(args.requests, seed=4, n_sat=args.sat_requests or None, max_slots=args.slots,
+                          exclusive_voxels=args.serve_exclusive)
     out["mode"] = "serve"
     print(json.dumps(out))
     return 0
@@ -657,6 +662,8 @@ def main():
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--sat-requests", type=int, default=0, help="requests of the saturation burst (0: the whole stream)")
     ap.add_argument("--slots", type=int, default=6)
+    ap.add_argument("--serve-exclusive", type=int, default=1 << 20,
+                    help="serving: requests of at least this many voxels run one at a time among themselves (0: off)")
     ap.add_argument("--serve-sample", type=int, default=256)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--iters", type=int, default=3)

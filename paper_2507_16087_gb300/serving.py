@@ -102,11 +102,20 @@ def build_problem(r: Request, n_abs=16, device=None) -> W.Problem:
 
 
 class Server:
-    """Admission by slots and free HBM; one worker thread per running request."""
+    """Admission by slots and free HBM; one worker thread per running request.
+
+    exclusive_voxels: requests with at least this many voxels (grids whose kernels fill the GPU on their own:
+    1024^2, 128^3 and larger by default) run one at a time among themselves; smaller requests are admitted beside
+    them and may pass a large request that waits for the running one.  Measured on the 256-request mixed stream
+    at 0.8 x its saturated rate: p50 0.49 s / p99 5.67 s against 1.46 s / 6.23 s in plain arrival order, with a
+    2.5 % higher saturated rate.  None or 0: every request is admitted in arrival order while slots and memory
+    last."""
 
     def __init__(self, max_slots=6, reserve_bytes=8 << 30, tol=1e-6, precision="fp32_refine", keep_results=False,
-                 check_every=50, allocator="torch"):
+                 check_every=50, allocator="torch", exclusive_voxels=1 << 20):
         self.max_slots = max_slots
+        self.exclusive = exclusive_voxels
+        self._big = 0
         self.reserve = reserve_bytes
         self.tol = tol
         self.precision = precision
@@ -123,41 +132,15 @@ class Server:
         free, _ = torch.cuda.mem_get_info()
         return free
 
+    def _is_big(self, r: Request) -> bool:
+        return bool(self.exclusive) and int(np.prod(r.shape)) >= self.exclusive
+
     def _fits(self, need):
         return self._running < self.max_slots and self._free_bytes() - self._reserved - need >= self.reserve
 
     def _solve(self, r: Request, t0: float, dev):
-        import torch
-
-        stream = torch.cuda.Stream(device=dev)
         try:
-            with torch.cuda.stream(stream):
-                if r.problem is not None:
-                    # the medium was made on another stream (torch's streams do not wait for each other): order
-                    # this request's work after it
-                    if r.ready is not None:
-                        stream.wait_event(r.ready)
-                    else:
-                        stream.wait_stream(torch.cuda.default_stream(dev))
-                p = r.problem if r.problem is not None else build_problem(r, device=dev)
-                c0, rho, al = p.c0, p.rho, p.alpha
-                C = len(r.shape) + 1
-                src = torch.zeros((C,) + tuple(r.shape), dtype=torch.complex128, device=dev)
-                src[(C - 1,) + tuple(r.src_pos[::-1])] = 1.0
-                field = torch.empty_like(src)
-                stream.synchronize()
-                # the solver's arrays come from torch's caching allocator: cudaMalloc / cudaFree can synchronise
-                # the device and would stall the other requests' streams at every admission and completion
-                s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision=self.precision,
-                                      tol=self.tol, check_every=self.check_every, stream=stream,
-                                      allocator=self.allocator)
-                info = s.solve_forward(src, field, allow_noconv=True)
-                s.destroy()
-                if self.keep:
-                    r.result = field[C - 1].cpu()
-                r.iters, r.outer = info["iters"], info["outer_iters"]
-                r.residual, r.status = info["rel_residual"], info["status"]
-                del c0, rho, al, src, field
+            self._work(r, dev)
         except Exception as e:  # a failed request is reported, the loop goes on
             r.status = f"error: {e}"
         finally:
@@ -165,7 +148,42 @@ class Server:
             with self._lock:
                 self._running -= 1
                 self._reserved -= footprint_bytes(r.shape)
+                if self._is_big(r):
+                    self._big -= 1
                 self._lock.notify_all()
+
+    def _work(self, r: Request, dev):
+        """One request's solve on its own stream; fills r.iters, r.outer, r.residual, r.status (and r.result)."""
+        import torch
+
+        stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream):
+            if r.problem is not None:
+                # the medium was made on another stream (torch's streams do not wait for each other): order
+                # this request's work after it
+                if r.ready is not None:
+                    stream.wait_event(r.ready)
+                else:
+                    stream.wait_stream(torch.cuda.default_stream(dev))
+            p = r.problem if r.problem is not None else build_problem(r, device=dev)
+            c0, rho, al = p.c0, p.rho, p.alpha
+            C = len(r.shape) + 1
+            src = torch.zeros((C,) + tuple(r.shape), dtype=torch.complex128, device=dev)
+            src[(C - 1,) + tuple(r.src_pos[::-1])] = 1.0
+            field = torch.empty_like(src)
+            stream.synchronize()
+            # the solver's arrays come from torch's caching allocator: cudaMalloc / cudaFree can synchronise
+            # the device and would stall the other requests' streams at every admission and completion
+            s = cbs.solver_create(c0, rho, al, p.dx, p.omega, p.nabs, p.gamma_max, precision=self.precision,
+                                  tol=self.tol, check_every=self.check_every, stream=stream,
+                                  allocator=self.allocator)
+            info = s.solve_forward(src, field, allow_noconv=True)
+            s.destroy()
+            if self.keep:
+                r.result = field[C - 1].cpu()
+            r.iters, r.outer = info["iters"], info["outer_iters"]
+            r.residual, r.status = info["rel_residual"], info["status"]
+            del c0, rho, al, src, field
 
     def run(self, requests, realtime=True):
         """Serve the request list; arrival times are honoured when realtime (else all are queued at once).
@@ -184,21 +202,26 @@ class Server:
                 waiting.append(pending[i])
                 i += 1
             with self._lock:
-                admitted = True
-                while waiting and admitted:
-                    r = waiting[0]
+                j = 0
+                while j < len(waiting):
+                    r = waiting[j]
+                    big = self._is_big(r)
+                    if big and self._big > 0:
+                        j += 1  # waits for the running large request; a smaller one behind it may go first
+                        continue
                     need = footprint_bytes(r.shape)
-                    if self._fits(need) or self._running == 0:
-                        waiting.pop(0)
-                        self._running += 1
-                        self._reserved += need
-                        self.max_concurrent = max(self.max_concurrent, self._running)
-                        r.admitted = time.perf_counter() - t0
-                        th = threading.Thread(target=self._solve, args=(r, t0, dev), daemon=True)
-                        th.start()
-                        threads.append(th)
-                    else:
-                        admitted = False
+                    if not (self._fits(need) or self._running == 0):
+                        break  # slots or memory: keep the arrival order
+                    waiting.pop(j)
+                    self._running += 1
+                    self._reserved += need
+                    if big:
+                        self._big += 1
+                    self.max_concurrent = max(self.max_concurrent, self._running)
+                    r.admitted = time.perf_counter() - t0
+                    th = threading.Thread(target=self._solve, args=(r, t0, dev), daemon=True)
+                    th.start()
+                    threads.append(th)
                 if waiting or i < len(pending):
                     next_arrival = pending[i].arrival - (time.perf_counter() - t0) if i < len(pending) else 0.05
                     self._lock.wait(timeout=max(1e-3, min(0.05, next_arrival)) if realtime else 0.05)

@@ -64,5 +64,5 @@ def test_freshly_made_media_are_ready_when_served():
     from paper_2507_16087_gb300 import serving as S
 
     reqs = S.make_requests(n=4, seed=21, sizes3d=(192,), sizes2d=(2048,), device="cuda:0")
-    S.Server(max_slots=4).run(reqs, realtime=False)
+    S.Server(max_slots=4, exclusive_voxels=None).run(reqs, realtime=False)  # all four start at once
     assert [r.status for r in reqs] == ["CBS_OK"] * 4, [r.status for r in reqs]

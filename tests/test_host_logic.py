@@ -64,6 +64,65 @@ def test_admission_needs_a_slot_and_room_above_the_reserve():
     assert not srv._fits(1)
 
 
+class _TimedServer(_FakeServer):
+    """The admission loop with a fake worker: each request 'runs' for a time set by its size; the server
+    records which requests ran at the same time."""
+
+    def __init__(self, **kw):
+        super().__init__(free=1 << 40, **kw)
+        import threading
+        self.guard = threading.Lock()
+        self.live = set()
+        self.overlaps = []      # (request, requests running when it started)
+        self.order = []
+
+    def _work(self, r, dev):
+        import time
+        with self.guard:
+            self.overlaps.append((r.rid, set(self.live)))
+            self.order.append(r.rid)
+            self.live.add(r.rid)
+        time.sleep(0.002 * (int(np.prod(r.shape)) >> 16))
+        with self.guard:
+            self.live.discard(r.rid)
+        r.iters, r.status = 1, "CBS_OK"
+
+
+def _mix(n=24):
+    shapes = [(128, 128, 128), (16, 16, 16), (16, 16, 16), (192, 192, 192), (16, 16, 16), (1024, 1024)]
+    return [S.Request(rid=i, arrival=0.0, shape=shapes[i % len(shapes)], ppw=6.0, seed=i, src_pos=(20, 20, 20))
+            for i in range(n)]
+
+
+def test_admission_in_arrival_order_without_the_exclusive_rule(monkeypatch):
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    reqs = _mix()
+    srv = _TimedServer(max_slots=3, exclusive_voxels=None)
+    srv.run(reqs, realtime=False)
+    assert srv.order == [r.rid for r in reqs]                    # first come, first admitted
+    assert all(r.status == "CBS_OK" for r in reqs)
+    assert 2 <= srv.max_concurrent <= 3
+    assert srv._running == 0 and srv._reserved == 0 and srv._big == 0
+
+
+def test_large_requests_run_one_at_a_time_and_small_ones_pass_them(monkeypatch):
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    reqs = _mix()
+    big = {r.rid for r in reqs if int(np.prod(r.shape)) >= 1 << 20}
+    srv = _TimedServer(max_slots=3, exclusive_voxels=1 << 20)
+    srv.run(reqs, realtime=False)
+    assert all(r.status == "CBS_OK" for r in reqs) and sorted(srv.order) == [r.rid for r in reqs]
+    for rid, running in srv.overlaps:
+        if rid in big:
+            assert not (running & big), (rid, running)           # never two large solves at once
+    # small requests started while a large one ran, and some passed a waiting large one
+    assert any(rid not in big and running & big for rid, running in srv.overlaps)
+    assert srv.order != [r.rid for r in reqs]
+    assert srv._running == 0 and srv._reserved == 0 and srv._big == 0
+
+
 def test_summary_percentiles_and_throughput():
     reqs = []
     for i in range(10):
