@@ -394,18 +394,26 @@ def run_gpu(args):
     hs = torch.from_numpy(np.ascontiguousarray(p.source)).pin_memory()
     hout = torch.empty((4,) + p.shape, dtype=torch.complex128).pin_memory()
     e2e_t = []
-    for k in range(2):
+    side = torch.cuda.Stream(device=dev)
+    for k in range(3):  # the last one is timed in the steady state: its device tensors reuse freed cached blocks
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        cur = torch.cuda.current_stream()
         dc = [a.to(dev, non_blocking=True) for a in hc]
-        ds = hs.to(dev, non_blocking=True)
+        # the source is needed only by the solve: its copy runs on a side stream while the solver is made
+        # (set-up reads only the medium)
+        with torch.cuda.stream(side):
+            ds = hs.to(dev, non_blocking=True)
         fld = torch.empty((4,) + p.shape, dtype=torch.complex128, device=dev)
         s = cbs.solver_create(dc[0], dc[1], dc[2], p.dx, p.omega, p.nabs, p.gamma_max, precision="fp32_refine", **kw)
+        cur.wait_stream(side)
+        ds.record_stream(cur)
         ie = s.solve_forward(ds, fld)
         hout.copy_(fld, non_blocking=True)
         torch.cuda.synchronize()
         s.destroy()
         e2e_t.append(time.perf_counter() - t0)
+        del dc, ds, fld, s
     h2d = sum(a.numel() * a.element_size() for a in hc) + hs.numel() * hs.element_size()
     d2h = hout.numel() * hout.element_size()
     e2e = {"value": Nv * ie["iters"] / e2e_t[-1], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
