@@ -30,8 +30,11 @@ def test_request_stream_is_seeded_and_well_formed():
     # mean inter-arrival time close to 1 / rate
     gaps = np.diff([0.0] + arrivals)
     assert abs(gaps.mean() - 0.2) < 0.08
-    # all at time zero without a rate
-    assert all(r.arrival == 0.0 for r in S.make_requests(n=8, seed=9, build=False))
+    # all at time zero without a rate, and the same requests as with one (the saturation burst and the Poisson
+    # stream of the serving bench are one request set)
+    c = S.make_requests(n=64, seed=9, build=False)
+    assert all(r.arrival == 0.0 for r in c)
+    assert [(r.shape, r.ppw, r.seed, r.src_pos, r.f_hz) for r in a] == [(r.shape, r.ppw, r.seed, r.src_pos, r.f_hz) for r in c]
 
 
 def test_footprint_grows_with_the_grid_and_covers_the_solver_arrays():
