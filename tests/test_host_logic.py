@@ -161,6 +161,42 @@ def test_bench_algorithmic_bytes_per_voxel():
     assert b2["rows_fwd"] == 3 * 8 * 3 + 2 * 4 + 2 * 4  # 2 rs + kp + et
 
 
+def _bench():
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    return bench
+
+
+def test_bench_model_bytes_and_fused_kernel_bytes():
+    bench = _bench()
+    m3 = bench.model_bytes_per_voxel(3, 4)
+    # the survey's byte model: x, y, medium (c, rho, alpha) in and w out = 4*8*3 + 12
+    assert m3["rows_fwd"] == m3["rows_inv"] == 108
+    assert m3["axis_fwd"] == m3["last_symbol"] == m3["axis_inv"] == 64
+    # fused update + next forward rows: w, x, y, medium in; x, w out
+    assert m3["rows_inv_fwd"] == 4 * 8 * 5 + 12 == 172
+    assert sum(m3[k] for k in ("axis_fwd", "last_symbol", "axis_inv", "rows_inv_fwd")) == 364
+    assert bench.kernel_bytes_per_voxel(3, 4)["rows_inv_fwd"] == 180  # medium as stored: 3 rs + kp + et
+    assert bench.model_bytes_per_voxel(3, 8)["rows_inv_fwd"] == 2 * 172  # float64 doubles every term
+
+
+def test_profile_traffic_is_used_only_on_the_sources_it_was_taken_on(tmp_path):
+    bench = _bench()
+    h = bench.sources_hash()
+    assert len(h) == 16 and h == bench.sources_hash()
+    good = tmp_path / "good.md"
+    good.write_text(f"text\ntraffic_bytes_per_launch sources={h}: rows_inv_fwd=301999360 last_symbol=68059392\n")
+    d, stale = bench.profile_traffic(str(good))
+    assert not stale and d == {"rows_inv_fwd": 301999360.0, "last_symbol": 68059392.0}
+    other = tmp_path / "other.md"
+    other.write_text("traffic_bytes_per_launch sources=0123456789abcdef: rows_inv_fwd=1\n")
+    assert bench.profile_traffic(str(other)) == ({}, True)
+    assert bench.profile_traffic(str(tmp_path / "missing.md")) == ({}, True)
+
+
 @pytest.mark.parametrize("n", [64, 96])
 def test_layered_inversion_workload_is_seeded_and_bounded(n):
     from paper_2507_16087_gb300 import workloads as W
