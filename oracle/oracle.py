@@ -16,8 +16,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "cbs_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "_build", "libcbs_oracle.so")
+# CBS_ORACLE_SRC / CBS_ORACLE_LIB: only the planted-mistake test sets them, in child processes, to run the pins
+# against a copy of this source with one deliberate slip (tests/test_oracle_mutants.py)
+_SRC = os.environ.get("CBS_ORACLE_SRC") or os.path.join(_HERE, "cbs_oracle.c")
+_LIB_PATH = os.environ.get("CBS_ORACLE_LIB") or os.path.join(_HERE, "_build", "libcbs_oracle.so")
 _lock = threading.Lock()
 _lib = None
 

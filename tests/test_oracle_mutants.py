@@ -1,0 +1,134 @@
+"""The oracle's pins catch plausible mistakes in it.
+
+Each mutant below is a copy of the oracle's C source with one planted slip of the kind the pins are meant to catch:
+a dropped term, a flipped sign, a wrong index, a transposed operand.  The copy is compiled on the CPU into a
+library of its own, and the oracle's pin tests run against it in a child process (the oracle loader takes the copy's
+paths from CBS_ORACLE_SRC / CBS_ORACLE_LIB there); at least one pin must fail for every mutant.  The oracle's own
+source and library are never touched, and no GPU code is involved.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "cbs_oracle.c")
+# fast pin files first; a child stops at its first failure
+PINS = ["tests/test_oracle_operators.py", "tests/test_oracle_solve.py", "tests/test_oracle_fft.py",
+        "tests/test_oracle_gradient.py"]
+
+# (what the slip is and which passage it breaks, exact text in the oracle, planted text)
+MUTANTS = [
+    ("complex sound speed with the absorption term's sign flipped (eq. 118)",
+     "c0[i] * c0[i] / (1.0 - 2.0 * I * alpha[i] * c0[i] / omega)",
+     "c0[i] * c0[i] / (1.0 + 2.0 * I * alpha[i] * c0[i] / omega)"),
+    ("staggered density taken at the cell itself instead of the two-point mean (App. B.1)",
+     "0.5 * (rho[i] + rho[neighbour_plus(i, eta, ndim, n)])",
+     "rho[i]"),
+    ("velocity diagonal without the absorbing layer: S+ rho * i omega (App. B.1)",
+     "d[eta * N + i] = rs * (gs + I * omega);",
+     "d[eta * N + i] = rs * (I * omega);"),
+    ("pressure diagonal with rho c^2 multiplied instead of divided (eq. HH1stOrderSH)",
+     "q[i] = (I * omega + g) * P->inv_rho_c2[i];",
+     "q[i] = (I * omega + g) / P->inv_rho_c2[i];"),
+    ("midrange shift whose imaginary part is taken from the real parts (Algorithm 1 preprocessing)",
+     "return 0.5 * (rmin + rmax) + I * 0.5 * (imin + imax);",
+     "return 0.5 * (rmin + rmax) + I * 0.5 * (rmin + rmax);"),
+    ("lambda = max deviation times beta instead of divided by it (eq. C)",
+     "P->lam1 = m1 > 0 ? m1 / beta : cabs(P->a1);",
+     "P->lam1 = m1 > 0 ? m1 * beta : cabs(P->a1);"),
+    ("pressure block of V scaled by lambda1 (wrong index, eq. LV)",
+     "P->v[ndim * N + i] = (q[i] - P->a2) / P->lam2;",
+     "P->v[ndim * N + i] = (q[i] - P->a2) / P->lam1;"),
+    ("wavenumbers without the negative half of fftfreq",
+     "long f = (j < (L + 1) / 2) ? j : j - L;",
+     "long f = j;"),
+    ("pressure source scaled by lambda1^-1/2 (wrong index, Sec. 2.3.1)",
+     "s[D * N + i] * P->inv_rho_c2[i]) * r2;",
+     "s[D * N + i] * P->inv_rho_c2[i]) * r1;"),
+    ("velocity source without the staggered density (eq. HH1stOrderSH)",
+     "P->rho_stag[eta * N + i] * s[eta * N + i]) * r1;",
+     "s[eta * N + i]) * r1;"),
+    ("(L+I)^-1 without the half-cell shift filters (App. B.1)",
+     "S[e] = P->collocated ? 1.0 : cexp(I * kv[e] * P->dx / 2.0);",
+     "S[e] = 1.0;"),
+    ("(L+I)^-1 diagonal with mu in place of mu - k_eta^2 (dropped term, App. B.1)",
+     "G[e][f] = l0 * (mu - kv[e] * kv[e]) / ((a + l0) * mu);",
+     "G[e][f] = l0 * mu / ((a + l0) * mu);"),
+    ("(L+I)^-1 off-diagonal velocity block with the shifts transposed (App. B.1)",
+     "(S[e] * conj(S[f]))",
+     "(conj(S[e]) * S[f])"),
+    ("(L+I)^-1 pressure row without the conjugate shift (transposed operand, App. B.1)",
+     "G[D][e] = -I * kv[e] * sq * conj(S[e]) / mu;",
+     "G[D][e] = -I * kv[e] * sq * S[e] / mu;"),
+    ("(L+I)^-1 pressure entry with lambda1 for lambda2 (wrong index, App. B.1)",
+     "G[D][D] = l1 * (a + l0) / mu;",
+     "G[D][D] = l0 * (a + l0) / mu;"),
+    ("L symbol's velocity row with the derivative sign flipped (eq. LV)",
+     "Lm[e][D] = I * kv[e] * Se / sq;",
+     "Lm[e][D] = -I * kv[e] * Se / sq;"),
+    ("adjoint apply without the conjugate transpose (M instead of M^H)",
+     "(mode >= 2 ? conj(M[c][r]) : M[r][c])",
+     "(mode >= 2 ? M[r][c] : M[r][c])"),
+    ("A_s x without the potential V x (dropped term, eq. LV)",
+     "out[i] += (adjoint ? conj(P->v[i]) : P->v[i]) * x[i];",
+     "out[i] += 0.0 * x[i];"),
+    ("pre-FFT fuse B x - y (flipped sign, eq. BornAlt)",
+     "w[i] = B * x[i] + y[i];",
+     "w[i] = B * x[i] - y[i];"),
+    ("Born update without B (dropped factor, eq. BornAlt)",
+     "cplx delta = nu * B * (z[i] - x[i]);",
+     "cplx delta = nu * (z[i] - x[i]);"),
+    ("true residual y + A_s x (flipped sign)",
+     "r[i] = y[i] - r[i];",
+     "r[i] = y[i] + r[i];"),
+    ("FFT combination step with the root index missing its stride (own FFT)",
+     "acc += tw[((q * k) % n) * step] * scratch[q * m + (k % m)];",
+     "acc += tw[(q * k) % n] * scratch[q * m + (k % m)];"),
+    ("inverse FFT without the 1/N factor (own FFT)",
+     "double s = 1.0 / (double)total;",
+     "double s = 1.0;"),
+]
+
+
+def _run_mutant(k, tmp):
+    """Plant mutant k (k < 0: the unchanged source, as a control), build it, run the pins on it in a child.
+    Returns (pytest exit code, first failing test, output tail)."""
+    src = open(SRC).read()
+    mutant = src if k < 0 else src.replace(MUTANTS[k][1], MUTANTS[k][2])
+    tag = "control" if k < 0 else f"mutant{k}"
+    path = os.path.join(tmp, f"{tag}.c")
+    lib = os.path.join(tmp, f"lib{tag}.so")
+    with open(path, "w") as f:
+        f.write(mutant)
+    # built here, so that a child's failure is a pin's verdict and never a build error
+    b = subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", path, "-o", lib, "-lm"],
+                       capture_output=True, text=True)
+    assert b.returncode == 0, (tag, b.stderr[-600:])
+    env = dict(os.environ, CBS_ORACLE_SRC=path, CBS_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    out = r.stdout + r.stderr
+    first = next((ln.split()[1] for ln in out.splitlines() if ln.startswith("FAILED ")), "")
+    return r.returncode, first, out[-600:]
+
+
+def test_mutants_are_well_defined():
+    src = open(SRC).read()
+    for desc, old, new in MUTANTS:
+        assert src.count(old) == 1, desc       # each slip is planted at exactly one place
+        assert old != new
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    workers = max(1, min(6, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda k: _run_mutant(k, str(tmp_path)), range(-1, len(MUTANTS))))
+    control, results = results[0], results[1:]
+    assert control[0] == 0, control[2]        # the harness itself passes the unchanged oracle
+    survivors = [(MUTANTS[k][0], out) for k, (rc, _, out) in enumerate(results) if rc == 0]
+    assert not survivors, survivors
+    # a child that could not collect or was interrupted (pytest exit codes 2-4) would not have tested the pins
+    for k, (rc, first, out) in enumerate(results):
+        assert rc == 1 and first, (MUTANTS[k][0], rc, out)
+        print(f"{MUTANTS[k][0]}: {first}")
