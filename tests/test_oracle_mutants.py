@@ -132,3 +132,45 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     for k, (rc, first, out) in enumerate(results):
         assert rc == 1 and first, (MUTANTS[k][0], rc, out)
         print(f"{MUTANTS[k][0]}: {first}")
+
+
+# the gradient oracle (oracle/gradient.py, Sec. 2.3's adjoint-state formula) against its finite-difference pin
+GRAD_SRC = os.path.join(ROOT, "oracle", "gradient.py")
+GRAD_MUTANTS = [
+    ("d(c^2)/dc0 factor with the wrong sign on its real part", "fac = -2.0 / c0 ** 3", "fac = 2.0 / c0 ** 3"),
+    ("staggered density's second neighbour dropped", "np.real(term + np.roll(term, 1, axis=ax))",
+     "np.real(term)"),
+    ("staggered density's second neighbour on the wrong side", "np.roll(term, 1, axis=ax)",
+     "np.roll(term, -1, axis=ax)"),
+    ("adjoint field not conjugated in the c0 term", "grad_c += np.real(np.conj(lp) *", "grad_c += np.real(lp *"),
+    ("dq/drho with the wrong sign", "(-bp / rho + q / rho * p)", "(-bp / rho - q / rho * p)"),
+]
+
+
+def _gradient_module(text):
+    import types
+
+    mod = types.ModuleType("oracle.gradient_planted")
+    mod.__package__ = "oracle"
+    exec(compile(text, GRAD_SRC, "exec"), mod.__dict__)
+    return mod
+
+
+def test_planted_mistakes_in_the_gradient_oracle_fail_its_pin(monkeypatch):
+    import test_oracle_gradient as TG
+
+    src = open(GRAD_SRC).read()
+
+    def pin_fails(text):
+        monkeypatch.setattr(TG, "gradient", _gradient_module(text))
+        try:
+            for which in ("c0", "rho"):
+                TG.test_gradient_matches_central_differences_dense(which)
+        except AssertionError:
+            return True
+        return False
+
+    assert not pin_fails(src)                   # control: the unchanged formula passes the pin
+    for desc, old, new in GRAD_MUTANTS:
+        assert src.count(old) == 1, desc
+        assert pin_fails(src.replace(old, new)), desc
