@@ -174,3 +174,71 @@ def test_planted_mistakes_in_the_gradient_oracle_fail_its_pin(monkeypatch):
     for desc, old, new in GRAD_MUTANTS:
         assert src.count(old) == 1, desc
         assert pin_fails(src.replace(old, new)), desc
+
+
+# the plain definition (oracle/dense.py: the discrete system assembled densely), planted in a child process by a
+# plugin that loads a slipped copy as oracle.dense before the pins import it
+DENSE_SRC = os.path.join(ROOT, "oracle", "dense.py")
+DENSE_PINS = ["tests/test_oracle_operators.py", "tests/test_oracle_solve.py"]
+DENSE_MUTANTS = [
+    ("complex sound speed with the absorption term's sign flipped (eq. 118)",
+     "    c2 = c0 ** 2 / (1 - 2j * alpha * c0 / omega)\n    per_axis_c = []",
+     "    c2 = c0 ** 2 / (1 + 2j * alpha * c0 / omega)\n    per_axis_c = []"),
+    ("staggered density averaged with the neighbour on the wrong side (App. B.1)",
+     "np.roll(rho, -1, axis=D - 1 - eta)", "np.roll(rho, 1, axis=D - 1 - eta)"),
+    ("forward staggered derivative with the backward half-cell shift (App. B.1)",
+     "dplus = Fi @ np.diag(1j * k * np.exp(1j * k * sh)) @ F",
+     "dplus = Fi @ np.diag(1j * k * np.exp(-1j * k * sh)) @ F"),
+    ("velocity rows coupled through the backward derivative (transposed blocks)",
+     "A[eta * N:(eta + 1) * N, D * N:] = axis_operator(shape, eta, dplus)",
+     "A[eta * N:(eta + 1) * N, D * N:] = axis_operator(shape, eta, dminus)"),
+    ("velocity source without the staggered density (eq. HH1stOrderSH)",
+     "out[eta] = rho_s[eta] * src[eta]", "out[eta] = src[eta]"),
+    ("absorbing layer evaluated at the cell centres for the staggered points (App. B.1)",
+     "0.0 if collocated else 0.5", "0.0"),
+    ("wavenumbers without the negative half of fftfreq",
+     "f = np.array([j if j < (n + 1) // 2 else j - n for j in range(n)], dtype=np.float64)",
+     "f = np.array([j for j in range(n)], dtype=np.float64)"),
+    ("pressure diagonal without the absorbing layer (eq. HH1stOrderSH)",
+     "q = (1j * omega + gamma) / (rho * c2)\n    d = []", "q = (1j * omega) / (rho * c2)\n    d = []"),
+]
+_PLUGIN = '''import importlib.util, os, sys
+import oracle
+_spec = importlib.util.spec_from_file_location("oracle.dense", os.environ["CBS_PLANTED_DENSE"])
+_mod = importlib.util.module_from_spec(_spec)
+sys.modules["oracle.dense"] = _mod
+_spec.loader.exec_module(_mod)
+oracle.dense = _mod
+'''
+
+
+def _run_dense_mutant(k, tmp):
+    src = open(DENSE_SRC).read()
+    text = src if k < 0 else src.replace(DENSE_MUTANTS[k][1], DENSE_MUTANTS[k][2])
+    tag = "dense_control" if k < 0 else f"dense{k}"
+    path = os.path.join(tmp, f"{tag}.py")
+    with open(path, "w") as f:
+        f.write(text)
+    with open(os.path.join(tmp, "planted_dense_plugin.py"), "w") as f:
+        f.write(_PLUGIN)
+    env = dict(os.environ, CBS_PLANTED_DENSE=path, OMP_NUM_THREADS="2",
+               PYTHONPATH=os.pathsep.join([tmp, ROOT, os.environ.get("PYTHONPATH", "")]))
+    r = subprocess.run([sys.executable, "-m", "pytest", *DENSE_PINS, "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
+                        "-p", "planted_dense_plugin"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    out = r.stdout + r.stderr
+    first = next((ln.split()[1] for ln in out.splitlines() if ln.startswith("FAILED ")), "")
+    return r.returncode, first, out[-600:]
+
+
+def test_planted_mistakes_in_the_plain_definition_fail_a_pin(tmp_path):
+    src = open(DENSE_SRC).read()
+    for desc, old, new in DENSE_MUTANTS:
+        assert src.count(old) == 1, desc
+    workers = max(1, min(6, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda k: _run_dense_mutant(k, str(tmp_path)), range(-1, len(DENSE_MUTANTS))))
+    control, results = results[0], results[1:]
+    assert control[0] == 0, control[2]
+    for k, (rc, first, out) in enumerate(results):
+        assert rc == 1 and first, (DENSE_MUTANTS[k][0], rc, out)
+        print(f"{DENSE_MUTANTS[k][0]}: {first}")
