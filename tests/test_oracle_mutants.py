@@ -88,6 +88,24 @@ MUTANTS = [
     ("inverse FFT without the 1/N factor (own FFT)",
      "double s = 1.0 / (double)total;",
      "double s = 1.0;"),
+    ("output pressure unscaled by lambda1^-1/2 (wrong index, Algorithm 1 output)",
+     "field[D * N + i] = x[D * N + i] * r2;",
+     "field[D * N + i] = x[D * N + i] * r1;"),
+    ("true residual without the square root",
+     "double rr = sqrt(norm2(r, CN) / norm2(y, CN));",
+     "double rr = norm2(r, CN) / norm2(y, CN);"),
+    ("Algorithm 1's increment not normalised by ||x||",
+     "if (incr) incr[it] = xx > 0 ? sqrt(dd / xx) : 0.0;",
+     "if (incr) incr[it] = xx > 0 ? sqrt(dd) : 0.0;"),
+    ("median of an even count taken as the upper middle value (Algorithm 1's example shift)",
+     "return (m % 2) ? v[m / 2] : 0.5 * (v[m / 2 - 1] + v[m / 2]);",
+     "return v[m / 2];"),
+    ("minimum enclosing circle through two points centred on one of them (Sec. 4)",
+     "c = 0.5 * (pi + pj);",
+     "c = pi;"),
+    ("absorbing layer's inner edge one cell off on the high side",
+     "double t = (xi - (double)(N - 1 - n_hi)) / (double)n_hi;",
+     "double t = (xi - (double)(N - n_hi)) / (double)n_hi;"),
 ]
 
 

@@ -107,6 +107,23 @@ def test_residual_at_exit_and_vanishing_increment():
     assert inc[0] <= 1e-8
 
 
+def test_increment_is_relative_and_scale_free():
+    """Algorithm 1 stops on the relative increment ||x_{k+1} - x_k|| / ||x_{k+1}||: from a zero start x_1 - x_0 is
+    x_1 itself, so the first increment is exactly 1; and the iteration is linear in y, so a source scaled by s
+    scales every iterate by s and leaves every increment unchanged."""
+    shape = (12, 10)
+    p = _problem(shape, 21)
+    P = _oracle(p)
+    y = P.scale_source(W.random_source(shape, 22))
+    x, inc = P.iterate(y, n_iter=8)
+    assert abs(inc[0] - 1.0) <= 1e-14
+    assert np.all(inc[1:] > 0) and np.all(inc[1:] < 1)
+    s = 1e3 * (0.6 - 0.8j)
+    xs, incs = P.iterate(s * y, n_iter=8)
+    assert _rel(xs, s * x) <= 1e-12
+    assert np.allclose(incs, inc, rtol=1e-10, atol=0)
+
+
 @pytest.mark.parametrize("shape", [(32, 24), (12, 10, 8)])
 def test_uniform_medium_closed_form(shape):
     dx = W.grid_step(6.0)
