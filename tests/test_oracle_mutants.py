@@ -106,6 +106,24 @@ MUTANTS = [
     ("absorbing layer's inner edge one cell off on the high side",
      "double t = (xi - (double)(N - 1 - n_hi)) / (double)n_hi;",
      "double t = (xi - (double)(N - n_hi)) / (double)n_hi;"),
+    ("absorbing layer from the last axis only (gamma summed over axes, Sec. 2.1 reading)",
+     "g += layer_axis(xi[a], (long)n[a], nabs + 2 * a, gmax, power);",
+     "g = layer_axis(xi[a], (long)n[a], nabs + 2 * a, gmax, power);"),
+    ("symbol's mu without lambda2 (dropped term, App. B.1)",
+     "const cplx mu = k2 + (a + l0) * (b + l1);",
+     "const cplx mu = k2 + (a + l0) * b;"),
+    ("adjoint (L+I)^-1 applied as the forward one",
+     "fourier_apply(P, in, out, adjoint ? 2 : 0);",
+     "fourier_apply(P, in, out, 0);"),
+    ("adjoint A_s with V instead of conj(V)",
+     "out[i] += (adjoint ? conj(P->v[i]) : P->v[i]) * x[i];",
+     "out[i] += P->v[i] * x[i];"),
+    ("adjoint fuse with B instead of conj(B)",
+     "cplx B = 1.0 - (adjoint ? conj(P->v[i]) : P->v[i]);\n            w[i] = B * x[i] + y[i];",
+     "cplx B = 1.0 - P->v[i];\n            w[i] = B * x[i] + y[i];"),
+    ("solve loop stopping at ten times the tolerance",
+     "while (r > tol && it < max_iter) {",
+     "while (r > 10.0 * tol && it < max_iter) {"),
 ]
 
 
