@@ -212,10 +212,53 @@ def test_planted_mistakes_in_the_gradient_oracle_fail_its_pin(monkeypatch):
         assert pin_fails(src.replace(old, new)), desc
 
 
-# the plain definition (oracle/dense.py: the discrete system assembled densely), planted in a child process by a
-# plugin that loads a slipped copy as oracle.dense before the pins import it
-DENSE_SRC = os.path.join(ROOT, "oracle", "dense.py")
-DENSE_PINS = ["tests/test_oracle_operators.py", "tests/test_oracle_solve.py"]
+# the Python parts of the oracle, planted in a child process by a plugin that loads a slipped copy of the module
+# (oracle.dense: the discrete system assembled densely; oracle.analytic: the free-space and series fields) before
+# the pins import it
+_PLUGIN = '''import importlib.util, os, sys
+import oracle
+_name = os.environ["CBS_PLANTED_MODULE"]
+_spec = importlib.util.spec_from_file_location(_name, os.environ["CBS_PLANTED_PATH"])
+_mod = importlib.util.module_from_spec(_spec)
+sys.modules[_name] = _mod
+_spec.loader.exec_module(_mod)
+setattr(oracle, _name.split(".")[1], _mod)
+'''
+
+
+def _run_module_mutant(module, src_path, pins, text, tag, tmp, select=()):
+    path = os.path.join(tmp, f"{tag}.py")
+    with open(path, "w") as f:
+        f.write(text)
+    with open(os.path.join(tmp, "planted_module_plugin.py"), "w") as f:
+        f.write(_PLUGIN)
+    env = dict(os.environ, CBS_PLANTED_MODULE=module, CBS_PLANTED_PATH=path, OMP_NUM_THREADS="2",
+               PYTHONPATH=os.pathsep.join([tmp, ROOT, os.environ.get("PYTHONPATH", "")]))
+    r = subprocess.run([sys.executable, "-m", "pytest", *pins, *select, "-x", "-q", "-m", "not gpu", "-p",
+                        "no:cacheprovider", "-p", "planted_module_plugin"], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=900)
+    out = r.stdout + r.stderr
+    first = next((ln.split()[1] for ln in out.splitlines() if ln.startswith("FAILED ")), "")
+    return r.returncode, first, out[-600:]
+
+
+def _check_module_mutants(module, src_path, pins, mutants, tmp, select=()):
+    src = open(src_path).read()
+    for desc, old, new in mutants:
+        assert src.count(old) == 1, desc
+    texts = [src] + [src.replace(old, new) for _, old, new in mutants]
+    tags = [f"{module.split('.')[1]}_control"] + [f"{module.split('.')[1]}{k}" for k in range(len(mutants))]
+    workers = max(1, min(6, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda k: _run_module_mutant(module, src_path, pins, texts[k], tags[k], tmp, select),
+                              range(len(texts))))
+    control, results = results[0], results[1:]
+    assert control[0] == 0, control[2]
+    for k, (rc, first, out) in enumerate(results):
+        assert rc == 1 and first, (mutants[k][0], rc, out)
+        print(f"{mutants[k][0]}: {first}")
+
+
 DENSE_MUTANTS = [
     ("complex sound speed with the absorption term's sign flipped (eq. 118)",
      "    c2 = c0 ** 2 / (1 - 2j * alpha * c0 / omega)\n    per_axis_c = []",
@@ -238,43 +281,37 @@ DENSE_MUTANTS = [
     ("pressure diagonal without the absorbing layer (eq. HH1stOrderSH)",
      "q = (1j * omega + gamma) / (rho * c2)\n    d = []", "q = (1j * omega) / (rho * c2)\n    d = []"),
 ]
-_PLUGIN = '''import importlib.util, os, sys
-import oracle
-_spec = importlib.util.spec_from_file_location("oracle.dense", os.environ["CBS_PLANTED_DENSE"])
-_mod = importlib.util.module_from_spec(_spec)
-sys.modules["oracle.dense"] = _mod
-_spec.loader.exec_module(_mod)
-oracle.dense = _mod
-'''
-
-
-def _run_dense_mutant(k, tmp):
-    src = open(DENSE_SRC).read()
-    text = src if k < 0 else src.replace(DENSE_MUTANTS[k][1], DENSE_MUTANTS[k][2])
-    tag = "dense_control" if k < 0 else f"dense{k}"
-    path = os.path.join(tmp, f"{tag}.py")
-    with open(path, "w") as f:
-        f.write(text)
-    with open(os.path.join(tmp, "planted_dense_plugin.py"), "w") as f:
-        f.write(_PLUGIN)
-    env = dict(os.environ, CBS_PLANTED_DENSE=path, OMP_NUM_THREADS="2",
-               PYTHONPATH=os.pathsep.join([tmp, ROOT, os.environ.get("PYTHONPATH", "")]))
-    r = subprocess.run([sys.executable, "-m", "pytest", *DENSE_PINS, "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
-                        "-p", "planted_dense_plugin"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    out = r.stdout + r.stderr
-    first = next((ln.split()[1] for ln in out.splitlines() if ln.startswith("FAILED ")), "")
-    return r.returncode, first, out[-600:]
 
 
 def test_planted_mistakes_in_the_plain_definition_fail_a_pin(tmp_path):
-    src = open(DENSE_SRC).read()
-    for desc, old, new in DENSE_MUTANTS:
-        assert src.count(old) == 1, desc
-    workers = max(1, min(6, (os.cpu_count() or 2) // 2))
-    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        results = list(ex.map(lambda k: _run_dense_mutant(k, str(tmp_path)), range(-1, len(DENSE_MUTANTS))))
-    control, results = results[0], results[1:]
-    assert control[0] == 0, control[2]
-    for k, (rc, first, out) in enumerate(results):
-        assert rc == 1 and first, (DENSE_MUTANTS[k][0], rc, out)
-        print(f"{DENSE_MUTANTS[k][0]}: {first}")
+    _check_module_mutants("oracle.dense", os.path.join(ROOT, "oracle", "dense.py"),
+                          ["tests/test_oracle_operators.py", "tests/test_oracle_solve.py"], DENSE_MUTANTS, str(tmp_path))
+
+
+ANALYTIC_MUTANTS = [
+    ("spherical Hankel function of the first kind (the wrong time convention)",
+     "special.spherical_jn(m, z, derivative=derivative) - 1j * special.spherical_yn(m, z, derivative=derivative)",
+     "special.spherical_jn(m, z, derivative=derivative) + 1j * special.spherical_yn(m, z, derivative=derivative)"),
+    ("3D point source normalised by dx^2 instead of dx^3",
+     "(1j * omega * S * dx ** 3 / c ** 2) * np.exp(-1j * k * R) / (4 * np.pi * R)",
+     "(1j * omega * S * dx ** 2 / c ** 2) * np.exp(-1j * k * R) / (4 * np.pi * R)"),
+    ("2D Green's function with +i/4 instead of -i/4",
+     "(1j * omega * S * dx ** 2 / c ** 2) * (-0.25j) * H2(0, k * R)",
+     "(1j * omega * S * dx ** 2 / c ** 2) * (0.25j) * H2(0, k * R)"),
+    ("sphere monopole coefficient at the sphere radius instead of the source distance (App. C reading)",
+     "        L = amp * (-1j * k0 / (4 * np.pi)) * h2(m, k0 * r_s)\n        M = np.array",
+     "        L = amp * (-1j * k0 / (4 * np.pi)) * h2(m, k0 * a)\n        M = np.array"),
+    ("disc interior velocity with the exterior impedance (App. C)",
+     "-special.jvp(m, k1 * a) / Z1]", "-special.jvp(m, k1 * a) / Z0]"),
+    ("disc plane-wave expansion without the Neumann factor",
+     "        inc = (1.0 if m == 0 else 2.0) * (-1j) ** m\n", "        inc = (-1j) ** m\n"),
+    ("scatterer's complex sound speed with the absorption term's sign flipped (eq. 118)",
+     "np.sqrt(c0 ** 2 / (1 - 2j * alpha * c0 / omega))", "np.sqrt(c0 ** 2 / (1 + 2j * alpha * c0 / omega))"),
+]
+
+
+def test_planted_mistakes_in_the_analytic_fields_fail_a_pin(tmp_path):
+    # the two slow refinement studies (1-D interface, disc) are left out: the series and point-source pins decide
+    _check_module_mutants("oracle.analytic", os.path.join(ROOT, "oracle", "analytic.py"),
+                          ["tests/test_oracle_physics.py"], ANALYTIC_MUTANTS, str(tmp_path),
+                          select=("-k", "not reflection_coefficient and not disc_scattering"))

@@ -23,6 +23,26 @@ from paper_2507_16087_gb300 import workloads as W
 OM = 2 * np.pi * W.F0
 
 
+# --------------------------------------------------------- absorption (eq. 118)
+def test_complex_sound_speed_attenuates_at_alpha():
+    """alpha is an amplitude attenuation in Np/m: with the complex sound speed of eq. 118 and outgoing waves
+    e^{-ikx} (e^{+i omega t}), the wavenumber k = omega / c has Im k = -alpha to first order in
+    eps = alpha c0 / omega (the next term is eps^2 / 2 relative), so the wave decays as e^{-alpha x}, and
+    Re k = omega / c0 to the same order.  Checked for the series' c and for the plain definition's c^2."""
+    from oracle import dense
+
+    c0 = 1500.0
+    for alpha in (1.0, 10.0, 50.0):
+        eps = alpha * c0 / OM
+        one = np.full((2, 2), 1.0)
+        _, _, _, c2 = dense.diagonals(c0 * one, 1000.0 * one, alpha * one, 1e-4, OM, ((0, 0), (0, 0)), 0.0)
+        for c in (A.complex_c(c0, alpha, OM), np.sqrt(c2[0, 0])):
+            k = OM / c
+            assert k.imag < 0
+            assert abs(-k.imag - alpha) <= eps ** 2 * alpha
+            assert abs(k.real - OM / c0) <= eps ** 2 * OM / c0
+
+
 # ------------------------------------------------------------ series self-checks
 def test_sphere_incident_series_is_point_source():
     rng = np.random.default_rng(1)
