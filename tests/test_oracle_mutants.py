@@ -180,6 +180,11 @@ GRAD_MUTANTS = [
      "np.roll(term, -1, axis=ax)"),
     ("adjoint field not conjugated in the c0 term", "grad_c += np.real(np.conj(lp) *", "grad_c += np.real(lp *"),
     ("dq/drho with the wrong sign", "(-bp / rho + q / rho * p)", "(-bp / rho - q / rho * p)"),
+    ("misfit without its factor 1/2 (adjoint source no longer its derivative)",
+     "J = 0.5 * float(np.sum(np.abs(r) ** 2))", "J = float(np.sum(np.abs(r) ** 2))"),
+    ("staggered layer values taken at the cell centres in the density derivative",
+     "stag.append(dense.layer_profile(n, nabs[a][0], nabs[a][1], gamma_max, power, 0.5).reshape(sh))",
+     "stag.append(dense.layer_profile(n, nabs[a][0], nabs[a][1], gamma_max, power, 0.0).reshape(sh))"),
 ]
 
 
